@@ -1,0 +1,185 @@
+/*
+ * pdnqp.h -- C ABI of the GB300 PDNQP solver.
+ *
+ * PDNQP ("PDNQP: A GPU-based Factorization-free Method for Large-scale
+ * Nonconvex Quadratic Programming", Chen & Lu) finds a stationary point of
+ *
+ *     min  c'x + 1/2 x'Qx   s.t.  l_c <= A x <= u_c,   l_x <= x <= u_x      (Eq. qp)
+ *
+ * with Q symmetric and possibly indefinite, by a proximal augmented-
+ * Lagrangian outer loop (Algorithm 3) whose strongly convex residual-form
+ * subproblems (Eq. prox-alm-subproblem / inner-qp) are solved on the GPU by
+ * restarted accelerated PDHG (Algorithm 4).  A row with l_c == u_c is an
+ * equality row (A_E x = b_E); every other row is an inequality row whose
+ * slack lives in [l_c, u_c] (for u_c = +inf this is A_I x >= b_I, Eq. qp).
+ *
+ * Conventions shared by every call:
+ *   - All pointers passed to pdnqp_create / pdnqp_get / pdnqp_set_start are
+ *     HOST pointers.  The library copies what it needs; the caller keeps
+ *     ownership of its arrays and may free them after the call returns.
+ *   - +-INFINITY marks an absent bound; any |v| >= 1e20 is treated as infinite.
+ *   - CSR matrices use 0-based int32 indices, row_ptr[n_rows] == nnz, column
+ *     indices in [0, n_cols).  Q must be square (n x n) and symmetric with BOTH
+ *     triangles stored; duplicates are not allowed.
+ *   - Return values: >= 0 is a solver status (pdnqp_solve) or success (0);
+ *     < 0 is an error code.  No C++ exception crosses this boundary.  The text
+ *     of the last error is available from pdnqp_last_error (per handle, or
+ *     thread-local when the handle is NULL).
+ *   - Every computation of the method runs in the library's CUDA kernels on
+ *     the current CUDA device; there is no CPU fallback.  A missing or unusable
+ *     GPU makes pdnqp_create fail with PDNQP_ERR_CUDA.
+ */
+#ifndef PDNQP_H
+#define PDNQP_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PDNQP_API __attribute__((visibility("default")))
+#else
+#define PDNQP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Solver statuses (Algorithm 3: solved, infeasibility, limits; Algorithm 4:
+ * numerical error when the rejection limit of Eq. adaptive-condition is hit). */
+#define PDNQP_SOLVED 0
+#define PDNQP_PRIMAL_INFEASIBLE 1
+#define PDNQP_DUAL_INFEASIBLE 2
+#define PDNQP_ITER_LIMIT 3
+#define PDNQP_TIME_LIMIT 4
+#define PDNQP_NUMERICAL_ERROR 5
+
+/* Error codes. */
+#define PDNQP_ERR_ARG (-1)           /* bad pointer, size or parameter name */
+#define PDNQP_ERR_BOUNDS (-2)        /* l > u somewhere, or NaN data */
+#define PDNQP_ERR_NOT_SYMMETRIC (-3) /* Q is not square/symmetric with both triangles */
+#define PDNQP_ERR_CUDA (-4)          /* CUDA runtime failure (message has the detail) */
+#define PDNQP_ERR_OOM (-5)           /* device allocation failed */
+#define PDNQP_ERR_STATE (-6)         /* call not valid in the handle's current state */
+
+/* Arithmetic of the hot path (option "precision"). */
+#define PDNQP_FP64 64      /* plain form: every vector, matrix value and sum in FP64 */
+#define PDNQP_FP32_BULK 32 /* SpMVs and vector updates in FP32; acceptance sums, restart/termination
+                              reductions, multiplier/penalty updates and the proximal-shift check in FP64 */
+
+typedef struct pdnqp pdnqp_t;
+
+/* Host CSR matrix. */
+typedef struct {
+  int32_t n_rows;
+  int32_t n_cols;
+  int64_t nnz;
+  const int32_t *row_ptr; /* n_rows + 1 entries */
+  const int32_t *col_idx; /* nnz entries */
+  const double *val;      /* nnz entries */
+} pdnqp_csr;
+
+/* Residuals of Eq. outer-residuals / outer-scales evaluated on the ORIGINAL
+ * (unscaled) data, with variable-bound violations counted in r_p (the external
+ * test of Sec. 4.1), plus counters. */
+typedef struct {
+  double r_p, r_d, s_p, s_d;
+  double rel_kkt;            /* max(r_p / (1 + s_p), r_d / (1 + s_d)) */
+  int64_t outer_iters;       /* Algorithm 3 iterations */
+  int64_t inner_iters;       /* accepted Algorithm 4 iterations, all solves */
+  int64_t trials;            /* trial steps (accepted + rejected) */
+  int64_t restarts;
+  int64_t kkt_passes;        /* inner matrix passes (3 SpMVs per trial, 2 per check) */
+  double solve_seconds;      /* wall time of the last pdnqp_solve */
+  double gamma;              /* proximal step of Eq. R-choice (scaled problem) */
+  double lambda_min;         /* Lanczos estimate of lambda_min of the scaled Q */
+  double obj;                /* c'x + 1/2 x'Qx at the returned x */
+} pdnqp_residuals;
+
+/* Creation options (pdnqp_create uses precision = PDNQP_FP64, device = current,
+ * stream = the legacy default stream). */
+typedef struct {
+  int32_t precision; /* PDNQP_FP64 or PDNQP_FP32_BULK */
+  int32_t device;    /* CUDA device ordinal, or -1 for the current device */
+  void *stream;      /* cudaStream_t all work is issued on; NULL = default stream */
+} pdnqp_options;
+
+/* Builds a solver for Eq. qp.  Copies and validates the inputs, orders the
+ * rows equality-first, builds CSR A, A^T and Q (diagonal made explicit) on the
+ * device once (Sec. 3.4, "Fixed sparse matrices"), applies the outer Ruiz
+ * scaling and objective scalar (Sec. 3.1, Eq. scaled-problem) and chooses the
+ * proximal step gamma (Eq. R-choice, FP64 Lanczos).  Sizes: Q is n x n, c has
+ * n entries, A is m x n (m may be 0; then A may be NULL), l_c/u_c have m
+ * entries, l_x/u_x n entries.  On success *out owns all device memory and 0 is
+ * returned; on failure *out is NULL and a negative code is returned. */
+PDNQP_API int pdnqp_create(pdnqp_t **out, const pdnqp_csr *Q, const double *c, const pdnqp_csr *A, const double *l_c,
+                 const double *u_c, const double *l_x, const double *u_x);
+PDNQP_API int pdnqp_create_ex(pdnqp_t **out, const pdnqp_csr *Q, const double *c, const pdnqp_csr *A, const double *l_c,
+                    const double *u_c, const double *l_x, const double *u_x, const pdnqp_options *opt);
+
+/* Frees the handle and its device memory.  NULL is accepted. */
+PDNQP_API void pdnqp_destroy(pdnqp_t *h);
+
+/* Runs Algorithm 3 (outer proximal ALM) with the GPU inner solver until the
+ * unscaled residuals meet r_p <= eps_abs + eps_rel s_p and r_d <= eps_abs +
+ * eps_rel s_d (Eq. outer-termination), or a limit is hit.  Starts from the
+ * point given by pdnqp_set_start (default x0 = 0 projected on the box,
+ * multipliers 0).  Returns a PDNQP_* status (>= 0) or an error code (< 0).
+ * Calling it again restarts from the start point. */
+PDNQP_API int pdnqp_solve(pdnqp_t *h, double eps_abs, double eps_rel);
+
+/* Copies the result of the last pdnqp_solve: x (n entries, original
+ * coordinates) and y (m entries, original row order, sign convention of Eq.
+ * kkt-stationarity: 0 in Qx + c + A'y + N(x), so y <= 0 on rows active at
+ * l_c and y >= 0 on rows active at u_c).  Any of x, y, r may be NULL. */
+PDNQP_API int pdnqp_get(const pdnqp_t *h, double *x, double *y, pdnqp_residuals *r);
+
+/* Warm start for the next pdnqp_solve (Sec. 3.2.1: user-provided x0, lambda0).
+ * x0 has n entries (original coordinates) or is NULL (zero); y0 has m entries
+ * in original row order and the sign convention of pdnqp_get, or is NULL. */
+PDNQP_API int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0);
+
+/* Sets / reads an algorithm parameter (Table tab:parameters plus the
+ * readings of unspecified rules).  Names: time_limit, k_out, k_in,
+ * sigma_init, theta_sigma, delta_gamma, rho_in_min, rho_in_max, rho_z,
+ * ruiz_outer (applies to the next pdnqp_create only; read-only here),
+ * ruiz_inner, k_chk, beta_suff, beta_nec, beta_art, rej_limit, kappa_shrink,
+ * delta_sigma, sigma_max, tol_floor, gamma (override, > 0; setting it
+ * replaces the Lanczos choice), chunk (trial slots per CUDA-graph launch).
+ * Returns PDNQP_ERR_ARG for an unknown name or an out-of-range value. */
+PDNQP_API int pdnqp_set_param(pdnqp_t *h, const char *name, double value);
+PDNQP_API int pdnqp_get_param(const pdnqp_t *h, const char *name, double *value);
+
+/* Problem sizes after classification: out[0..4] = n, m, m_E, m_I, nnz(Q with
+ * explicit diagonal). */
+PDNQP_API int pdnqp_dims(const pdnqp_t *h, int64_t *out5);
+
+/* Text of the last error on this handle (or of this thread when h is NULL). */
+PDNQP_API const char *pdnqp_last_error(const pdnqp_t *h);
+
+/* Test hook for per-step parity.  Performs the setup of outer iteration 0
+ * from the start point and runs its inner solve (Algorithm 4) with the
+ * inner termination test ignored, writing a snapshot after each of the
+ * n_ckpt accepted-iteration counts in ckpt (strictly increasing, >= 1).
+ * Snapshot layout, doubles: [w (dw) | y (m) | wbar (dw) | ybar (m) | omega,
+ * kappa, t, t_total, trials, restarts, kkt_restart, kkt_last], with dw =
+ * n + m_I + m, w = (x, s_I, r_E, r_I) and y in the outer-scaled,
+ * inner-unscaled coordinates of Eq. inner-qp, rows equality-first.  snap must
+ * hold n_ckpt * (2 (dw + m) + 8) doubles (host memory).  Returns the number of
+ * snapshots written, or a negative code. */
+PDNQP_API int pdnqp_debug_inner(pdnqp_t *h, int n_ckpt, const int64_t *ckpt, double *snap);
+
+/* Measurement hook: replays one hot-path kernel `reps` times on the handle's
+ * stream with the state left by the last solve (which = 0: the fused Q/A^T
+ * SpMV + acceptance kernel, 1: the fused A SpMV + dual-step kernel, 2: the
+ * primal step).  The replays write only trial buffers.  Returns 0 or an error. */
+PDNQP_API int pdnqp_replay_kernel(pdnqp_t *h, int which, int reps);
+
+/* Algorithmic (compulsory) DRAM bytes of one launch of the kernel `which`
+ * (same numbering as pdnqp_replay_kernel) and of one accepted iteration
+ * (which = -1), for the roofline. */
+PDNQP_API int pdnqp_kernel_bytes(const pdnqp_t *h, int which, double *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDNQP_H */

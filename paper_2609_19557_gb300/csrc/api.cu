@@ -1,0 +1,445 @@
+// C ABI of the PDNQP solver (include/pdnqp.h): input validation, row
+// classification (equality rows first), CSR construction on the host (Q with
+// an explicit diagonal, A^T by counting sort), and dispatch to the FP64 or
+// FP32-bulk device solver.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/pdnqp.h"
+#include "solver.cuh"
+
+using pdq::HostProblem;
+using pdq::Params;
+using pdq::Result;
+using pdq::SolverBase;
+
+struct pdnqp {
+  SolverBase *solver = nullptr;
+  int n = 0, m = 0, mE = 0;
+  std::vector<int> perm;
+  Params prm;
+  std::string err;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int precision = PDNQP_FP64;
+  int64_t nnzq = 0;
+};
+
+static thread_local std::string g_err;
+
+static int fail(pdnqp_t *h, int code, const std::string &msg) {
+  if (h) h->err = msg;
+  g_err = msg;
+  return code;
+}
+
+static double clean_bound(double v) {
+  if (v >= 1e20) return INFINITY;
+  if (v <= -1e20) return -INFINITY;
+  return v;
+}
+
+// Validates a host CSR matrix; returns its rows with columns sorted.
+static int read_csr(const pdnqp_csr *M, int rows, int cols, const char *name, std::vector<int> &rp,
+                    std::vector<int> &ci, std::vector<double> &v, std::string &msg) {
+  if (!M) {
+    msg = std::string(name) + " is NULL";
+    return PDNQP_ERR_ARG;
+  }
+  if (M->n_rows != rows || M->n_cols != cols) {
+    msg = std::string(name) + " has the wrong shape";
+    return PDNQP_ERR_ARG;
+  }
+  if (M->nnz < 0 || M->nnz > 2147483647LL || (M->nnz > 0 && (!M->col_idx || !M->val)) || !M->row_ptr) {
+    msg = std::string(name) + ": bad nnz or NULL arrays";
+    return PDNQP_ERR_ARG;
+  }
+  if (M->row_ptr[0] != 0 || M->row_ptr[rows] != M->nnz) {
+    msg = std::string(name) + ": row_ptr[0] must be 0 and row_ptr[n_rows] == nnz";
+    return PDNQP_ERR_ARG;
+  }
+  rp.assign(rows + 1, 0);
+  ci.resize(M->nnz);
+  v.resize(M->nnz);
+  std::vector<std::pair<int, double>> tmp;
+  for (int i = 0; i < rows; ++i) {
+    const int b = M->row_ptr[i], e = M->row_ptr[i + 1];
+    if (e < b) {
+      msg = std::string(name) + ": row_ptr not monotone";
+      return PDNQP_ERR_ARG;
+    }
+    tmp.clear();
+    for (int k = b; k < e; ++k) {
+      const int c = M->col_idx[k];
+      if (c < 0 || c >= cols) {
+        msg = std::string(name) + ": column index out of range";
+        return PDNQP_ERR_ARG;
+      }
+      if (!std::isfinite(M->val[k])) {
+        msg = std::string(name) + ": non-finite value";
+        return PDNQP_ERR_BOUNDS;
+      }
+      tmp.push_back({c, M->val[k]});
+    }
+    std::sort(tmp.begin(), tmp.end(), [](const std::pair<int, double> &a, const std::pair<int, double> &b2) {
+      return a.first < b2.first;
+    });
+    for (size_t k = 1; k < tmp.size(); ++k)
+      if (tmp[k].first == tmp[k - 1].first) {
+        msg = std::string(name) + ": duplicate entry";
+        return PDNQP_ERR_ARG;
+      }
+    for (size_t k = 0; k < tmp.size(); ++k) {
+      ci[b + k] = tmp[k].first;
+      v[b + k] = tmp[k].second;
+    }
+    rp[i + 1] = e;
+  }
+  return 0;
+}
+
+static void transpose(int rows, int cols, const std::vector<int> &rp, const std::vector<int> &ci,
+                      const std::vector<double> &v, std::vector<int> &trp, std::vector<int> &tci,
+                      std::vector<double> &tv) {
+  trp.assign(cols + 1, 0);
+  tci.resize(ci.size());
+  tv.resize(v.size());
+  for (int c : ci) trp[c + 1]++;
+  for (int i = 0; i < cols; ++i) trp[i + 1] += trp[i];
+  std::vector<int> pos(trp.begin(), trp.end() - 1);
+  for (int i = 0; i < rows; ++i)
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      const int d = pos[ci[k]]++;
+      tci[d] = i;
+      tv[d] = v[k];
+    }
+}
+
+static int prepare(const pdnqp_csr *Q, const double *c, const pdnqp_csr *A, const double *l_c, const double *u_c,
+                   const double *l_x, const double *u_x, HostProblem &P, std::string &msg) {
+  if (!Q || !c || !l_x || !u_x) {
+    msg = "NULL argument";
+    return PDNQP_ERR_ARG;
+  }
+  const int n = Q->n_rows;
+  const int m = A ? A->n_rows : 0;
+  if (n <= 0 || Q->n_cols != n) {
+    msg = "Q must be square with n >= 1";
+    return PDNQP_ERR_NOT_SYMMETRIC;
+  }
+  if (m < 0 || (m > 0 && (!l_c || !u_c))) {
+    msg = "row bounds missing";
+    return PDNQP_ERR_ARG;
+  }
+  P.n = n;
+  P.m = m;
+  std::vector<int> qrp, qci;
+  std::vector<double> qv;
+  int rc = read_csr(Q, n, n, "Q", qrp, qci, qv, msg);
+  if (rc) return rc;
+  {  // symmetry: the transpose of the sorted CSR must be identical
+    std::vector<int> trp, tci;
+    std::vector<double> tv;
+    transpose(n, n, qrp, qci, qv, trp, tci, tv);
+    if (trp != qrp || tci != qci || tv != qv) {
+      msg = "Q is not symmetric with both triangles stored";
+      return PDNQP_ERR_NOT_SYMMETRIC;
+    }
+  }
+  // Q with an explicit diagonal entry in every row.
+  P.q_rp.assign(n + 1, 0);
+  P.q_diag.assign(n, 0);
+  P.q_ci.clear();
+  P.q_v.clear();
+  P.q_ci.reserve(qci.size() + n);
+  P.q_v.reserve(qci.size() + n);
+  for (int i = 0; i < n; ++i) {
+    bool done = false;
+    for (int k = qrp[i]; k < qrp[i + 1]; ++k) {
+      if (!done && qci[k] >= i) {
+        if (qci[k] != i) {
+          P.q_diag[i] = (int)P.q_ci.size();
+          P.q_ci.push_back(i);
+          P.q_v.push_back(0.0);
+        } else {
+          P.q_diag[i] = (int)P.q_ci.size();
+        }
+        done = true;
+      }
+      P.q_ci.push_back(qci[k]);
+      P.q_v.push_back(qv[k]);
+    }
+    if (!done) {
+      P.q_diag[i] = (int)P.q_ci.size();
+      P.q_ci.push_back(i);
+      P.q_v.push_back(0.0);
+    }
+    P.q_rp[i + 1] = (int)P.q_ci.size();
+  }
+  P.c.assign(c, c + n);
+  P.lx.resize(n);
+  P.ux.resize(n);
+  for (int i = 0; i < n; ++i) {
+    if (!std::isfinite(c[i])) {
+      msg = "c has a non-finite entry";
+      return PDNQP_ERR_BOUNDS;
+    }
+    const double lo = clean_bound(l_x[i]), hi = clean_bound(u_x[i]);
+    if (std::isnan(lo) || std::isnan(hi) || lo > hi || lo == INFINITY || hi == -INFINITY) {
+      msg = "variable bounds: need l_x <= u_x (no NaN)";
+      return PDNQP_ERR_BOUNDS;
+    }
+    P.lx[i] = lo;
+    P.ux[i] = hi;
+  }
+  // Rows: classify and order equality rows first (stable).
+  std::vector<int> arp, aci;
+  std::vector<double> av;
+  if (m > 0) {
+    rc = read_csr(A, m, n, "A", arp, aci, av, msg);
+    if (rc) return rc;
+  }
+  P.perm.clear();
+  std::vector<double> lo(m), hi(m);
+  for (int j = 0; j < m; ++j) {
+    lo[j] = clean_bound(l_c[j]);
+    hi[j] = clean_bound(u_c[j]);
+    if (std::isnan(lo[j]) || std::isnan(hi[j]) || lo[j] > hi[j] || lo[j] == INFINITY || hi[j] == -INFINITY) {
+      msg = "row bounds: need l_c <= u_c (no NaN, no infinite equality)";
+      return PDNQP_ERR_BOUNDS;
+    }
+  }
+  for (int j = 0; j < m; ++j)
+    if (lo[j] == hi[j]) P.perm.push_back(j);
+  P.mE = (int)P.perm.size();
+  for (int j = 0; j < m; ++j)
+    if (lo[j] != hi[j]) P.perm.push_back(j);
+  P.a_rp.assign(m + 1, 0);
+  P.a_ci.clear();
+  P.a_v.clear();
+  P.lc.resize(m);
+  P.uc.resize(m);
+  for (int r = 0; r < m; ++r) {
+    const int j = P.perm[r];
+    for (int k = arp[j]; k < arp[j + 1]; ++k) {
+      P.a_ci.push_back(aci[k]);
+      P.a_v.push_back(av[k]);
+    }
+    P.a_rp[r + 1] = (int)P.a_ci.size();
+    P.lc[r] = lo[j];
+    P.uc[r] = hi[j];
+  }
+  transpose(m, n, P.a_rp, P.a_ci, P.a_v, P.at_rp, P.at_ci, P.at_v);
+  return 0;
+}
+
+extern "C" {
+
+int pdnqp_create_ex(pdnqp_t **out, const pdnqp_csr *Q, const double *c, const pdnqp_csr *A, const double *l_c,
+                    const double *u_c, const double *l_x, const double *u_x, const pdnqp_options *opt) {
+  if (!out) return fail(nullptr, PDNQP_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  pdnqp_options o = {PDNQP_FP64, -1, nullptr};
+  if (opt) o = *opt;
+  if (o.precision != PDNQP_FP64 && o.precision != PDNQP_FP32_BULK)
+    return fail(nullptr, PDNQP_ERR_ARG, "precision must be PDNQP_FP64 or PDNQP_FP32_BULK");
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0)
+    return fail(nullptr, PDNQP_ERR_CUDA,
+                std::string("no usable CUDA device: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "0 devices"));
+  if (o.device >= 0) {
+    e = cudaSetDevice(o.device);
+    if (e != cudaSuccess) return fail(nullptr, PDNQP_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  }
+  HostProblem P;
+  std::string msg;
+  int rc = prepare(Q, c, A, l_c, u_c, l_x, u_x, P, msg);
+  if (rc) return fail(nullptr, rc, msg);
+  pdnqp_t *h = new (std::nothrow) pdnqp_t();
+  if (!h) return fail(nullptr, PDNQP_ERR_OOM, "host allocation failed");
+  h->n = P.n;
+  h->m = P.m;
+  h->mE = P.mE;
+  h->perm = P.perm;
+  h->stream = (cudaStream_t)o.stream;
+  cudaGetDevice(&h->device);
+  h->precision = o.precision;
+  h->nnzq = (int64_t)P.q_ci.size();
+  h->solver = o.precision == PDNQP_FP64 ? pdq::make_solver_f64(h->stream) : pdq::make_solver_f32(h->stream);
+  rc = h->solver->setup(P, h->prm, &msg);
+  if (rc < 0) {
+    fail(nullptr, rc, msg);
+    delete h->solver;
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return 0;
+}
+
+int pdnqp_create(pdnqp_t **out, const pdnqp_csr *Q, const double *c, const pdnqp_csr *A, const double *l_c,
+                 const double *u_c, const double *l_x, const double *u_x) {
+  return pdnqp_create_ex(out, Q, c, A, l_c, u_c, l_x, u_x, nullptr);
+}
+
+void pdnqp_destroy(pdnqp_t *h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  delete h->solver;
+  delete h;
+}
+
+int pdnqp_solve(pdnqp_t *h, double eps_abs, double eps_rel) {
+  if (!h) return fail(nullptr, PDNQP_ERR_ARG, "handle is NULL");
+  if (!(eps_abs >= 0) || !(eps_rel >= 0)) return fail(h, PDNQP_ERR_ARG, "tolerances must be >= 0");
+  cudaSetDevice(h->device);
+  std::string msg;
+  int rc = h->solver->solve(eps_abs, eps_rel, h->prm, &msg);
+  if (rc < 0) return fail(h, rc, msg);
+  return rc;
+}
+
+int pdnqp_get(const pdnqp_t *h, double *x, double *y, pdnqp_residuals *r) {
+  if (!h) return fail(nullptr, PDNQP_ERR_ARG, "handle is NULL");
+  cudaSetDevice(h->device);
+  Result R;
+  std::vector<double> lam_int(y ? h->m : 0);
+  int rc = h->solver->get(x, y ? lam_int.data() : nullptr, &R);
+  if (rc < 0) return fail(const_cast<pdnqp_t *>(h), rc, "pdnqp_get: no solution yet or CUDA failure");
+  if (y)
+    for (int k = 0; k < h->m; ++k) y[h->perm[k]] = lam_int[k];
+  if (r) {
+    r->r_p = R.rp;
+    r->r_d = R.rd;
+    r->s_p = R.sp;
+    r->s_d = R.sd;
+    r->rel_kkt = R.rel_kkt;
+    r->outer_iters = R.outer;
+    r->inner_iters = R.inner;
+    r->trials = R.trials;
+    r->restarts = R.restarts;
+    r->kkt_passes = R.passes;
+    r->solve_seconds = R.seconds;
+    r->gamma = h->solver->gamma();
+    r->lambda_min = h->solver->lambda_min();
+    r->obj = R.obj;
+  }
+  return 0;
+}
+
+int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0) {
+  if (!h) return fail(nullptr, PDNQP_ERR_ARG, "handle is NULL");
+  std::vector<double> l0;
+  if (y0) {
+    l0.resize(h->m);
+    for (int k = 0; k < h->m; ++k) l0[k] = y0[h->perm[k]];
+    for (double v : l0)
+      if (!std::isfinite(v)) return fail(h, PDNQP_ERR_BOUNDS, "y0 has a non-finite entry");
+  }
+  if (x0)
+    for (int i = 0; i < h->n; ++i)
+      if (!std::isfinite(x0[i])) return fail(h, PDNQP_ERR_BOUNDS, "x0 has a non-finite entry");
+  return h->solver->set_start(x0, y0 ? l0.data() : nullptr);
+}
+
+#define PDNQP_PARAMS(X)                                                                           \
+  X(time_limit, d, 0.0, 1e300) X(k_out, ll, 1.0, 9.2e18) X(k_in, ll, 1.0, 9.2e18)                 \
+  X(sigma_init, d, 1e-300, 1e300) X(theta_sigma, d, 0.0, 1.0) X(delta_gamma, d, 1e-300, 1e300)    \
+  X(rho_in_min, d, 0.0, 1.0) X(rho_in_max, d, 0.0, 1.0) X(rho_z, d, 0.0, 1.0)                      \
+  X(ruiz_inner, i, 0.0, 1000.0) X(lanczos_steps, i, 1.0, 100000.0) X(k_chk, i, 1.0, 1e9)           \
+  X(beta_suff, d, 0.0, 1.0) X(beta_nec, d, 0.0, 1.0) X(beta_art, d, 0.0, 1.0)                      \
+  X(rej_limit, i, 1.0, 1e9) X(kappa_shrink, d, 1e-6, 0.999999) X(delta_sigma, d, 1.0, 1e300)       \
+  X(sigma_max, d, 1e-300, 1e300) X(tol_floor, d, 0.0, 1.0) X(chunk, i, 1.0, 4096.0)               \
+  X(g_rows, i, 0.0, 32.0) X(g_cols, i, 0.0, 32.0)
+
+int pdnqp_set_param(pdnqp_t *h, const char *name, double value) {
+  if (!h || !name) return fail(h, PDNQP_ERR_ARG, "NULL handle or name");
+  const std::string s(name);
+  if (s == "gamma") {
+    if (!(value > 0) || !std::isfinite(value)) return fail(h, PDNQP_ERR_ARG, "gamma must be > 0");
+    h->solver->set_gamma(value);
+    return 0;
+  }
+#define X(nm, kind, lo, hi)                                                              \
+  if (s == #nm) {                                                                        \
+    if (!(value >= (lo) && value <= (hi))) return fail(h, PDNQP_ERR_ARG, "out of range: " #nm); \
+    h->prm.nm = (decltype(h->prm.nm))value;                                              \
+    return 0;                                                                            \
+  }
+  PDNQP_PARAMS(X)
+#undef X
+  return fail(h, PDNQP_ERR_ARG, "unknown parameter: " + s);
+}
+
+int pdnqp_get_param(const pdnqp_t *h, const char *name, double *value) {
+  if (!h || !name || !value) return fail(nullptr, PDNQP_ERR_ARG, "NULL argument");
+  const std::string s(name);
+  if (s == "gamma") {
+    *value = h->solver->gamma();
+    return 0;
+  }
+  if (s == "ruiz_outer") {
+    *value = h->prm.ruiz_outer;
+    return 0;
+  }
+  if (s == "precision") {
+    *value = h->precision;
+    return 0;
+  }
+#define X(nm, kind, lo, hi) \
+  if (s == #nm) {           \
+    *value = (double)h->prm.nm; \
+    return 0;               \
+  }
+  PDNQP_PARAMS(X)
+#undef X
+  return fail(const_cast<pdnqp_t *>(h), PDNQP_ERR_ARG, "unknown parameter: " + s);
+}
+
+int pdnqp_dims(const pdnqp_t *h, int64_t *out5) {
+  if (!h || !out5) return fail(nullptr, PDNQP_ERR_ARG, "NULL argument");
+  out5[0] = h->n;
+  out5[1] = h->m;
+  out5[2] = h->mE;
+  out5[3] = h->m - h->mE;
+  out5[4] = h->nnzq;
+  return 0;
+}
+
+const char *pdnqp_last_error(const pdnqp_t *h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+int pdnqp_debug_inner(pdnqp_t *h, int n_ckpt, const int64_t *ckpt, double *snap) {
+  if (!h || n_ckpt < 0 || (n_ckpt > 0 && (!ckpt || !snap))) return fail(h, PDNQP_ERR_ARG, "bad arguments");
+  for (int k = 0; k < n_ckpt; ++k)
+    if (ckpt[k] < 1 || (k > 0 && ckpt[k] <= ckpt[k - 1]))
+      return fail(h, PDNQP_ERR_ARG, "checkpoints must be strictly increasing and >= 1");
+  cudaSetDevice(h->device);
+  std::string msg;
+  int rc = h->solver->debug_inner(h->prm, n_ckpt, ckpt, snap, &msg);
+  if (rc < 0) return fail(h, rc, msg);
+  return rc;
+}
+
+int pdnqp_replay_kernel(pdnqp_t *h, int which, int reps) {
+  if (!h || which < 0 || which > 2 || reps < 0) return fail(h, PDNQP_ERR_ARG, "bad arguments");
+  cudaSetDevice(h->device);
+  int rc = h->solver->replay(which, reps);
+  if (rc < 0) return fail(h, rc, "replay failed (solve first)");
+  return 0;
+}
+
+int pdnqp_kernel_bytes(const pdnqp_t *h, int which, double *bytes) {
+  if (!h || !bytes || which < -1 || which > 3) return fail(nullptr, PDNQP_ERR_ARG, "bad arguments");
+  *bytes = h->solver->kernel_bytes(which);
+  return 0;
+}
+
+}  // extern "C"

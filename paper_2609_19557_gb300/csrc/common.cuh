@@ -1,0 +1,180 @@
+// Device helpers shared by the PDNQP kernels: sub-warp row groups for CSR
+// SpMV, deterministic block reductions, and the device-resident scalar state
+// of the inner solver.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pdq {
+
+constexpr int kBlock = 256;        // threads per block of every vector/SpMV kernel
+constexpr int kMaxBlocks = 152 * 8;  // grid cap: 8 resident 256-thread blocks on each of 152 SMs
+constexpr int kRedThreads = 1024;  // threads of the single-block final reductions
+constexpr int kMaxPartials = 48;   // quantities reduced per launch (rows of the partials array)
+
+// Inner-solver status kept on the device (Algorithm 4 return paths).
+enum InnerStatus : int {
+  ST_RUNNING = 0,
+  ST_CONVERGED = 1,
+  ST_ITER_LIMIT = 2,
+  ST_NUMERICAL_ERROR = 3,
+  ST_PAUSED = 4,
+  ST_IDLE = 5,
+};
+
+// Scalar state of one inner solve.  Written by the host before the solve,
+// updated only by single-block kernels (decide / check-final), read by all.
+struct DevState {
+  int status;
+  int cur;             // index (0/1) of the current iterate buffers; the trial goes to 1 - cur
+  int accepted;        // the last trial was accepted: the new averages are in buffer acur ^ 1
+  int acur;            // index (0/1) of the committed running averages
+  int check_due;       // a stopping/restart check follows this trial
+  int restart_flag;    // the last check restarts the epoch
+  int restart_use_avg; // ... from the averaged candidate
+  int ret_avg;         // converged candidate is the average
+  int ignore_conv;     // debug: never stop on the inner termination test
+  long long t;         // accepted steps in the current epoch (N_p = N_d, Eq. pdqp-trial)
+  long long t_total;   // accepted steps in this inner solve
+  long long trials;    // all trials, all solves
+  long long accepted_all;
+  long long restarts;
+  long long rej;       // consecutive rejections
+  long long k_in;      // accepted-iteration limit (Table tab:parameters)
+  long long pause_at;  // debug: pause after this many accepted steps (-1: never)
+  long long k_chk;     // check period
+  long long rej_limit;
+  double kappa;        // common step factor of the rejection rule
+  double omega;        // primal weight (Eq. primal-weight-update)
+  double alpha_acc;    // alpha of the last accepted trial
+  double k_restart;    // restart metric at the start of the epoch
+  double k_last;       // restart metric of the candidate at the previous check
+  double dta, dtr;     // inner tolerances delta_a, delta_r
+  double shrink;       // kappa factor on rejection
+  double beta_suff, beta_nec, beta_art;
+  double chk[16];      // reductions of the last check (diagnostics)
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+template <int G, typename A>
+__device__ __forceinline__ A group_sum(A v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <int G, typename A>
+__device__ __forceinline__ A group_max(A v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block reduction of NQ doubles; kind[q] = 0 sum, 1 max.  Thread 0 writes
+// part[q * kMaxBlocks + blockIdx.x].  Must be called by every thread of the
+// block (kBlock threads).  Fixed order: deterministic for a fixed grid.
+template <int NQ>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NQ], const unsigned kind_mask, double *part) {
+  __shared__ double sm[NQ][kBlock / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double a = ((kind_mask >> q) & 1u) ? warp_max(v[q]) : warp_sum(v[q]);
+    if (lane == 0) sm[q][wid] = a;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const bool mx = (kind_mask >> q) & 1u;
+      double a = lane < kBlock / 32 ? sm[q][lane] : (mx ? 0.0 : 0.0);
+      a = mx ? warp_max(a) : warp_sum(a);
+      if (lane == 0) part[q * kMaxBlocks + blockIdx.x] = a;
+    }
+  }
+}
+
+// Single-block final reduction of NQ quantities over nb partials (fixed order).
+template <int NQ>
+__device__ __forceinline__ void final_reduce(const double *part, int nb, const unsigned kind_mask, double (&out)[NQ]) {
+  __shared__ double sm[NQ][kRedThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const bool mx = (kind_mask >> q) & 1u;
+    double a = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kRedThreads) {
+      double p = part[q * kMaxBlocks + b];
+      a = mx ? fmax(a, p) : a + p;
+    }
+    a = mx ? warp_max(a) : warp_sum(a);
+    if (lane == 0) sm[q][wid] = a;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const bool mx = (kind_mask >> q) & 1u;
+    double a = lane < kRedThreads / 32 ? sm[q][lane] : 0.0;
+    a = mx ? warp_max(a) : warp_sum(a);
+    out[q] = __shfl_sync(0xffffffffu, a, 0);
+  }
+  __syncthreads();
+}
+
+// Rows of a CSR matrix are processed by groups of G lanes (G divides 32).
+// Iteration is warp-uniform: every lane of a warp runs the same trips
+// (base is the same for the whole warp), with row >= nrows marking idle
+// groups, so group shuffles are always executed by the full warp.
+template <int G>
+struct GroupIter {
+  int lane_g, sub;
+  long long first, step;
+  __device__ __forceinline__ GroupIter() {
+    lane_g = threadIdx.x & (G - 1);
+    sub = (threadIdx.x & 31) / G;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    first = gw * (32 / G);
+    step = nw * (32 / G);
+  }
+};
+
+// Sum over the entries of one row of f(col, val), reduced over the group; every
+// lane of the group gets the result.
+template <int G, typename Acc, typename T, typename F>
+__device__ __forceinline__ Acc row_sum(const int *__restrict__ rp, const int *__restrict__ ci,
+                                       const T *__restrict__ val, long long row, bool valid, int lane_g, F f) {
+  Acc a = Acc(0);
+  if (valid) {
+    const int b = rp[row], e = rp[row + 1];
+    for (int k = b + lane_g; k < e; k += G) a += f(ci[k], val[k]);
+  }
+  return group_sum<G, Acc>(a);
+}
+template <int G, typename Acc, typename T, typename F>
+__device__ __forceinline__ Acc row_max(const int *__restrict__ rp, const int *__restrict__ ci,
+                                       const T *__restrict__ val, long long row, bool valid, int lane_g, F f) {
+  Acc a = Acc(0);
+  if (valid) {
+    const int b = rp[row], e = rp[row + 1];
+    for (int k = b + lane_g; k < e; k += G) a = fmax(a, f(ci[k], val[k]));
+  }
+  return group_max<G, Acc>(a);
+}
+
+inline int grid_for(long long work_items, int per_block) {
+  long long b = (work_items + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > kMaxBlocks) b = kMaxBlocks;
+  return (int)b;
+}
+
+}  // namespace pdq

@@ -1,0 +1,686 @@
+// CUDA kernels of the PDNQP hot path (Algorithm 4) and of its setup and outer
+// glue (Algorithm 3, Sec. 3.1), templated on the storage type T of the inner
+// iterates and matrix values (double: plain FP64 form; float: FP32-bulk form).
+//
+// Coordinates.  The inner iterates live in the outer-scaled, inner-UNSCALED
+// coordinates of Eq. inner-qp: w = (x, s_I, r_E, r_I), y.  The penalty scaling
+// (Eq. inner-penalty-scaling) and the inner Ruiz scaling (Sec. 3.3.2) are the
+// diagonal change of variables w = E w~, y = D y~; PDHG in the scaled space is
+// exactly PDHG in these coordinates with the effective diagonal steps
+// tau_eff = e^2 tau~ and eta_eff = d^2 eta~, and the acceptance test (Eq.
+// adaptive-condition) is invariant under it.  So the CSR values of A, A^T and
+// Q are never rewritten inside the solve: the scalings only enter the step
+// vectors and the scaled restart metric.
+//
+// H_k = diag(Q + gamma^-1 I, 0, sigma_E, sigma_I) and B = [[A_E, 0, -I, 0],
+// [A_I, -I, 0, -I]] are never formed: their s and r blocks are diagonal and
+// handled inline, and only the x blocks are SpMVs (Sec. 3.4: one product each
+// with Q, A and A^T per trial).
+#pragma once
+#include <math.h>
+
+#include "common.cuh"
+
+namespace pdq {
+namespace {  // internal linkage: each solver TU owns its kernels
+
+// Rows of the partial-sums array used by each reduction.
+constexpr int P_TR_R = 0;    // trial, row kernel: lhs, rhs_h, rhs_b
+constexpr int P_TR_C = 3;    // trial, column kernel
+constexpr int P_CK_R = 6;    // check, row kernel: 16 quantities
+constexpr int P_CK_C = 22;   // check, column kernel: 16 quantities
+constexpr unsigned CK_MAXMASK = 0x0F0Fu;  // quantities 0-3 and 8-11 of a check are maxima
+
+template <typename T>
+struct Mat {
+  int nrows;
+  const int *rp;
+  const int *ci;
+  const T *val;
+};
+
+// Device pointers of one solver (passed by value to the trial kernels).
+template <typename T>
+struct Dev {
+  int n, m, mE;
+  Mat<T> H, A, At;  // H = Qbar + gamma^-1 I (x block of H_k), A (rows E then I), A^T
+  // n-vectors
+  T *x[2], *Hx[2], *Aty[2], *xbar[2], *Hxbar[2];
+  T *qx, *lx, *ux, *taux, *ex, *xst, *Atybar;
+  // m-vectors (s is indexed by row; entries of equality rows are unused)
+  T *y[2], *s[2], *r[2], *Bw[2], *ybar[2], *sbar[2], *rbar[2];
+  T *eta, *taus, *taur, *es, *er, *dy, *h, *ls, *us, *yst, *sst, *rst, *Bwbar;
+  // FP64 outer data: multipliers lambda and row penalties sigma
+  const double *lam, *sig;
+  double *part;
+  DevState *st;
+};
+
+template <typename T>
+__device__ __forceinline__ T clampv(T v, T lo, T hi) {
+  // Same comparison order as a plain projection: NaN stays NaN.
+  v = v < lo ? lo : v;
+  v = v > hi ? hi : v;
+  return v;
+}
+
+#define PDNQP_GRID_STRIDE(i, N) \
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)(N); \
+       i += (long long)gridDim.x * blockDim.x)
+
+// ===========================================================================
+// Trial step (Eq. pdqp-trial) and acceptance test (Eq. adaptive-condition).
+// ===========================================================================
+
+// Primal x-block of the trial: x_tr = P_[l,u](x - tau (q + (1-alpha) H xbar +
+// alpha H x - A'y)) with the cached products H x, H xbar, A'y.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_primal(Dev<T> d) {
+  const DevState *st = d.st;
+  if (st->status != ST_RUNNING) return;
+  const int cur = st->cur, ab = st->acur ^ st->accepted;
+  const double t = (double)st->t;
+  const T alpha = T(2.0 / (t + 2.0));
+  const T oma = T(1) - alpha;
+  const T sc = T(st->kappa / st->omega);
+  const T *__restrict__ x = d.x[cur];
+  const T *__restrict__ Hx = d.Hx[cur];
+  const T *__restrict__ Aty = d.Aty[cur];
+  const T *__restrict__ Hxb = d.Hxbar[ab];
+  T *__restrict__ xt = d.x[1 - cur];
+  PDNQP_GRID_STRIDE(i, d.n) {
+    const T g = d.qx[i] + oma * Hxb[i] + alpha * Hx[i] - Aty[i];
+    xt[i] = clampv<T>(x[i] - (sc * d.taux[i]) * g, d.lx[i], d.ux[i]);
+  }
+}
+
+// Constraint rows: (A x_tr)_j, the s/r blocks of the primal trial, B w_tr,
+// the dual trial y_tr = y + eta (h - B w_tr - beta (B w_tr - B w)), and the
+// row-local terms of the acceptance sums.
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_rows(Dev<T> d) {
+  const DevState *st = d.st;
+  if (st->status != ST_RUNNING) return;
+  const int cur = st->cur, nx = 1 - cur, ab = st->acur ^ st->accepted;
+  const double t = (double)st->t;
+  const T alpha = T(2.0 / (t + 2.0)), oma = T(1) - alpha;
+  const T beta = T(t / (t + 1.0));
+  const T sct = T(st->kappa / st->omega), sce = T(st->kappa * st->omega);
+  const T *__restrict__ xt = d.x[nx];
+  double L = 0.0, RH = 0.0, RB = 0.0;
+  GroupIter<G> it;
+  for (long long base = it.first; base < d.m; base += it.step) {
+    const long long j = base + it.sub;
+    const bool valid = j < d.m;
+    const T ax = row_sum<G, T>(d.A.rp, d.A.ci, d.A.val, j, valid, it.lane_g,
+                               [&](int k, T a) { return a * xt[k]; });
+    if (valid && it.lane_g == 0) {
+      const T y = d.y[cur][j], r = d.r[cur][j], rb = d.rbar[ab][j];
+      const T lam = T(d.lam[j]), sig = T(d.sig[j]);
+      const T tr = sct * d.taur[j];
+      const T rt = r - tr * (lam + sig * (oma * rb + alpha * r) + y);
+      T bwt = ax - rt, ds = T(0), ts = T(1);
+      if (j >= d.mE) {
+        const T s = d.s[cur][j];
+        ts = sct * d.taus[j];
+        const T stv = clampv<T>(s - ts * y, d.ls[j], d.us[j]);
+        d.s[nx][j] = stv;
+        bwt -= stv;
+        ds = stv - s;
+      }
+      const T bw = d.Bw[cur][j];
+      const T et = sce * d.eta[j];
+      const T yt = y + et * (d.h[j] - bwt - beta * (bwt - bw));
+      d.r[nx][j] = rt;
+      d.Bw[nx][j] = bwt;
+      d.y[nx][j] = yt;
+      const double dr = double(rt - r), dyv = double(yt - y), dsv = double(ds);
+      L += dr * dr / double(tr) + dyv * dyv / double(et) + (j >= d.mE ? dsv * dsv / double(ts) : 0.0);
+      RH += fabs(dr * double(sig) * dr);
+      RB += fabs(dsv * dyv) + fabs(dr * dyv);
+    }
+  }
+  double v[3] = {L, RH, RB};
+  block_reduce_store<3>(v, 0u, d.part + P_TR_R * kMaxBlocks);
+}
+
+// Variable rows: (H x_tr)_i and (A' y_tr)_i (the products with Q and A^T),
+// plus the x terms of the acceptance sums.
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_cols(Dev<T> d) {
+  const DevState *st = d.st;
+  if (st->status != ST_RUNNING) return;
+  const int cur = st->cur, nx = 1 - cur;
+  const T sct = T(st->kappa / st->omega);
+  const T *__restrict__ xt = d.x[nx];
+  const T *__restrict__ yt = d.y[nx];
+  double L = 0.0, RH = 0.0, RB = 0.0;
+  GroupIter<G> it;
+  for (long long base = it.first; base < d.n; base += it.step) {
+    const long long i = base + it.sub;
+    const bool valid = i < d.n;
+    const T hx = row_sum<G, T>(d.H.rp, d.H.ci, d.H.val, i, valid, it.lane_g,
+                               [&](int k, T a) { return a * xt[k]; });
+    const T aty = row_sum<G, T>(d.At.rp, d.At.ci, d.At.val, i, valid, it.lane_g,
+                                [&](int k, T a) { return a * yt[k]; });
+    if (valid && it.lane_g == 0) {
+      d.Hx[nx][i] = hx;
+      d.Aty[nx][i] = aty;
+      const double dx = double(xt[i] - d.x[cur][i]);
+      const double dh = double(hx - d.Hx[cur][i]);
+      const double da = double(aty - d.Aty[cur][i]);
+      L += dx * dx / double(sct * d.taux[i]);
+      RH += fabs(dx * dh);
+      RB += fabs(dx * da);
+    }
+  }
+  double v[3] = {L, RH, RB};
+  block_reduce_store<3>(v, 0u, d.part + P_TR_C * kMaxBlocks);
+}
+
+// Acceptance decision (single block, deterministic order).  On acceptance the
+// trial buffers become current (index flip); on rejection both step vectors
+// are shrunk through kappa.
+__global__ void __launch_bounds__(kRedThreads) k_decide(DevState *st, const double *part, int nb_r, int nb_c) {
+  if (st->status != ST_RUNNING) return;
+  double a[3], b[3];
+  final_reduce<3>(part + P_TR_R * kMaxBlocks, nb_r, 0u, a);
+  final_reduce<3>(part + P_TR_C * kMaxBlocks, nb_c, 0u, b);
+  if (threadIdx.x != 0) return;
+  // Commit the averages computed after the previous acceptance.
+  st->acur ^= st->accepted;
+  st->accepted = 0;
+  st->restart_flag = 0;
+  st->check_due = 0;
+  st->trials += 1;
+  const double lhs = a[0] + b[0], rh = a[1] + b[1], rb = a[2] + b[2];
+  if (!isfinite(lhs) || !isfinite(rh) || !isfinite(rb)) {
+    st->status = ST_NUMERICAL_ERROR;
+    return;
+  }
+  if (0.5 * lhs >= 0.5 * rh + rb) {
+    st->alpha_acc = 2.0 / ((double)st->t + 2.0);
+    st->cur ^= 1;
+    st->accepted = 1;
+    st->t += 1;
+    st->t_total += 1;
+    st->accepted_all += 1;
+    st->rej = 0;
+    const bool due = (st->k_chk > 0 && st->t_total % st->k_chk == 0) || st->t_total == st->k_in;
+    st->check_due = due ? 1 : 0;
+    if (!due && st->t_total == st->pause_at) st->status = ST_PAUSED;
+  } else {
+    st->kappa *= st->shrink;
+    st->rej += 1;
+    if (st->rej >= st->rej_limit) st->status = ST_NUMERICAL_ERROR;
+  }
+}
+
+// Running averages after an acceptance: bar[acur^1] = (1 - alpha) bar[acur]
+// + alpha w (Algorithm 4, "update the weighted averages"), for x, H x, s, r, y.
+// Reads and writes different buffers, so a repeated launch is harmless.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_average(Dev<T> d) {
+  const DevState *st = d.st;
+  if (!st->accepted) return;
+  const int cur = st->cur, a0 = st->acur, a1 = st->acur ^ 1;
+  const T alpha = T(st->alpha_acc), oma = T(1) - alpha;
+  PDNQP_GRID_STRIDE(i, d.n) {
+    d.xbar[a1][i] = oma * d.xbar[a0][i] + alpha * d.x[cur][i];
+    d.Hxbar[a1][i] = oma * d.Hxbar[a0][i] + alpha * d.Hx[cur][i];
+  }
+  PDNQP_GRID_STRIDE(j, d.m) {
+    d.ybar[a1][j] = oma * d.ybar[a0][j] + alpha * d.y[cur][j];
+    d.rbar[a1][j] = oma * d.rbar[a0][j] + alpha * d.r[cur][j];
+    if (j >= d.mE) d.sbar[a1][j] = oma * d.sbar[a0][j] + alpha * d.s[cur][j];
+  }
+}
+
+// ===========================================================================
+// Periodic check (Sec. 3.3.3 inner termination; restart criteria and the
+// primal weight, Eqs. primal-weight-movement / primal-weight-update).
+// Per candidate (c = current, a = average) 8 quantities:
+//   0 r_p (max), 1 s_p (max), 2 r_d (max), 3 s_d (max),
+//   4 sum (d (Bw - h))^2, 5 sum ((w - P(w - e^2 g)) / e)^2,
+//   6 sum ((w - w_start) / e)^2, 7 sum ((y - y_start) / d)^2
+// stored as [c0..c7, a0..a7].  mode 1 = only the current point's 4 and 5
+// (restart metric of the inner start).
+// ===========================================================================
+template <typename T>
+struct RowCand {
+  // s/r/y contributions of one row to the 8 quantities of one candidate.
+  __device__ static void add(double *q, bool is_ineq, T bw, T h, T s, T r, T y, T lam, T sig, T ls, T us, T es,
+                             T er, T dyv, T sst, T rst, T yst) {
+    const double e_bh = double(bw) - double(h);
+    q[0] = fmax(q[0], fabs(e_bh));
+    q[1] = fmax(q[1], fmax(fabs(double(bw)), fabs(double(h))));
+    const double gr = double(sig) * double(r) + double(lam) + double(y);
+    q[2] = fmax(q[2], fabs(gr));
+    q[3] = fmax(q[3], fmax(fabs(double(sig) * double(r)), fmax(fabs(double(lam)), fabs(double(y)))));
+    q[4] += (double(dyv) * e_bh) * (double(dyv) * e_bh);
+    q[5] += (double(er) * gr) * (double(er) * gr);
+    const double wr = (double(r) - double(rst)) / double(er);
+    q[6] += wr * wr;
+    const double wy = (double(y) - double(yst)) / double(dyv);
+    q[7] += wy * wy;
+    if (is_ineq) {
+      const double gs = double(y);
+      const double sv = double(s);
+      const double lo = double(ls), hi = double(us);
+      double p = sv - gs;
+      p = p < lo ? lo : p;
+      p = p > hi ? hi : p;
+      q[2] = fmax(q[2], fabs(sv - p));
+      const double e2 = double(es) * double(es);
+      double p2 = sv - e2 * gs;
+      p2 = p2 < lo ? lo : p2;
+      p2 = p2 > hi ? hi : p2;
+      const double ks = (sv - p2) / double(es);
+      q[5] += ks * ks;
+      const double ws = (sv - double(sst)) / double(es);
+      q[6] += ws * ws;
+    }
+  }
+};
+
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_check_rows(Dev<T> d, int mode) {
+  const DevState *st = d.st;
+  if (mode == 0 && !(st->status == ST_RUNNING && st->check_due)) return;
+  const int cur = st->cur, ab = st->acur ^ st->accepted;
+  const T *__restrict__ xb = d.xbar[ab];
+  double q[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) q[k] = 0.0;
+  GroupIter<G> it;
+  for (long long base = it.first; base < d.m; base += it.step) {
+    const long long j = base + it.sub;
+    const bool valid = j < d.m;
+    T axb = T(0);
+    if (mode == 0)
+      axb = row_sum<G, T>(d.A.rp, d.A.ci, d.A.val, j, valid, it.lane_g, [&](int k, T a) { return a * xb[k]; });
+    if (valid && it.lane_g == 0) {
+      const bool ineq = j >= d.mE;
+      const T h = d.h[j], lam = T(d.lam[j]), sig = T(d.sig[j]);
+      const T ls = ineq ? d.ls[j] : T(0), us = ineq ? d.us[j] : T(0), es = ineq ? d.es[j] : T(1);
+      const T er = d.er[j], dyv = d.dy[j];
+      const T sst = ineq ? d.sst[j] : T(0), rst = d.rst[j], yst = d.yst[j];
+      const T sc = ineq ? d.s[cur][j] : T(0);
+      RowCand<T>::add(q, ineq, d.Bw[cur][j], h, sc, d.r[cur][j], d.y[cur][j], lam, sig, ls, us, es, er, dyv, sst,
+                      rst, yst);
+      if (mode == 0) {
+        const T sa = ineq ? d.sbar[ab][j] : T(0);
+        const T ra = d.rbar[ab][j];
+        const T bwa = axb - sa - ra;
+        d.Bwbar[j] = bwa;
+        RowCand<T>::add(q + 8, ineq, bwa, h, sa, ra, d.ybar[ab][j], lam, sig, ls, us, es, er, dyv, sst, rst, yst);
+      }
+    }
+  }
+  block_reduce_store<16>(q, CK_MAXMASK, d.part + P_CK_R * kMaxBlocks);
+}
+
+template <typename T>
+__device__ __forceinline__ void col_cand(double *q, T x, T hx, T aty, T qx, T lx, T ux, T ex, T xst) {
+  const double g = double(hx) + double(qx) - double(aty);
+  const double xv = double(x), lo = double(lx), hi = double(ux);
+  double p = xv - g;
+  p = p < lo ? lo : p;
+  p = p > hi ? hi : p;
+  q[2] = fmax(q[2], fabs(xv - p));
+  q[3] = fmax(q[3], fmax(fabs(double(hx)), fmax(fabs(double(qx)), fabs(double(aty)))));
+  const double e2 = double(ex) * double(ex);
+  double p2 = xv - e2 * g;
+  p2 = p2 < lo ? lo : p2;
+  p2 = p2 > hi ? hi : p2;
+  const double k = (xv - p2) / double(ex);
+  q[5] += k * k;
+  const double w = (xv - double(xst)) / double(ex);
+  q[6] += w * w;
+}
+
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_check_cols(Dev<T> d, int mode) {
+  const DevState *st = d.st;
+  if (mode == 0 && !(st->status == ST_RUNNING && st->check_due)) return;
+  const int cur = st->cur, ab = st->acur ^ st->accepted;
+  const T *__restrict__ yb = d.ybar[ab];
+  double q[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) q[k] = 0.0;
+  GroupIter<G> it;
+  for (long long base = it.first; base < d.n; base += it.step) {
+    const long long i = base + it.sub;
+    const bool valid = i < d.n;
+    T atyb = T(0);
+    if (mode == 0)
+      atyb = row_sum<G, T>(d.At.rp, d.At.ci, d.At.val, i, valid, it.lane_g, [&](int k, T a) { return a * yb[k]; });
+    if (valid && it.lane_g == 0) {
+      const T qx = d.qx[i], lx = d.lx[i], ux = d.ux[i], ex = d.ex[i], xst = d.xst[i];
+      col_cand<T>(q, d.x[cur][i], d.Hx[cur][i], d.Aty[cur][i], qx, lx, ux, ex, xst);
+      if (mode == 0) {
+        d.Atybar[i] = atyb;
+        col_cand<T>(q + 8, d.xbar[ab][i], d.Hxbar[ab][i], atyb, qx, lx, ux, ex, xst);
+      }
+    }
+  }
+  block_reduce_store<16>(q, CK_MAXMASK, d.part + P_CK_C * kMaxBlocks);
+}
+
+// Decisions of the check (single block): inner termination of both candidates
+// (Eq. inner-termination), iteration limit, restart criteria and primal weight.
+__global__ void __launch_bounds__(kRedThreads) k_check_final(DevState *st, const double *part, int nb_r, int nb_c) {
+  if (!(st->status == ST_RUNNING && st->check_due)) return;
+  double a[16], b[16];
+  final_reduce<16>(part + P_CK_R * kMaxBlocks, nb_r, CK_MAXMASK, a);
+  final_reduce<16>(part + P_CK_C * kMaxBlocks, nb_c, CK_MAXMASK, b);
+  if (threadIdx.x != 0) return;
+  double q[16];
+  for (int k = 0; k < 16; ++k) q[k] = ((CK_MAXMASK >> k) & 1u) ? fmax(a[k], b[k]) : a[k] + b[k];
+  for (int k = 0; k < 16; ++k) st->chk[k] = q[k];
+  // The averages computed after this trial's acceptance are committed here.
+  st->acur ^= st->accepted;
+  st->accepted = 0;
+  st->restart_flag = 0;
+  const double dta = st->dta, dtr = st->dtr;
+  const double spc = fmax(1.0, q[1]), sdc = fmax(1.0, q[3]);
+  const double spa = fmax(1.0, q[9]), sda = fmax(1.0, q[11]);
+  const bool okc = q[0] <= dta + dtr * spc && q[2] <= dta + dtr * sdc;
+  const bool oka = q[8] <= dta + dtr * spa && q[10] <= dta + dtr * sda;
+  if (!st->ignore_conv) {
+    if (okc) { st->status = ST_CONVERGED; st->ret_avg = 0; return; }
+    if (oka) { st->status = ST_CONVERGED; st->ret_avg = 1; return; }
+  }
+  if (st->t_total == st->k_in) { st->status = ST_ITER_LIMIT; return; }
+  const double om = st->omega;
+  const double kc = sqrt(om * q[4] + q[5] / om);
+  const double ka = sqrt(om * q[12] + q[13] / om);
+  const bool use_avg = ka < kc;
+  const double kcand = use_avg ? ka : kc;
+  const bool restart = kcand <= st->beta_suff * st->k_restart ||
+                       (kcand <= st->beta_nec * st->k_restart && kcand > st->k_last) ||
+                       (double)st->t >= st->beta_art * (double)st->t_total;
+  st->k_last = kcand;
+  if (restart) {
+    const double dW = sqrt(use_avg ? q[14] : q[6]);
+    const double dY = sqrt(use_avg ? q[15] : q[7]);
+    if (dW > 0.0 && dY > 0.0) st->omega = exp(0.25 * log(dY / dW) + 0.75 * log(om));
+    st->kappa = 1.0;
+    st->t = 0;
+    st->k_restart = kcand;
+    st->k_last = INFINITY;
+    st->restarts += 1;
+    st->restart_flag = 1;
+    st->restart_use_avg = use_avg ? 1 : 0;
+  }
+  if (st->t_total == st->pause_at) st->status = ST_PAUSED;
+}
+
+// Restart (Algorithm 4): optionally move the current point to the average
+// (with its cached products), then make it the epoch start and clear the
+// averages.  Idempotent, so a repeated launch is harmless.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_check_apply(Dev<T> d) {
+  const DevState *st = d.st;
+  if (!(st->check_due && st->restart_flag)) return;
+  const int cur = st->cur, ab = st->acur;
+  const bool ua = st->restart_use_avg;
+  PDNQP_GRID_STRIDE(i, d.n) {
+    T x = d.x[cur][i], hx = d.Hx[cur][i];
+    if (ua) {
+      x = d.xbar[ab][i];
+      hx = d.Hxbar[ab][i];
+      d.x[cur][i] = x;
+      d.Hx[cur][i] = hx;
+      d.Aty[cur][i] = d.Atybar[i];
+    }
+    d.xst[i] = x;
+    d.xbar[ab][i] = x;
+    d.Hxbar[ab][i] = hx;
+  }
+  PDNQP_GRID_STRIDE(j, d.m) {
+    T y = d.y[cur][j], r = d.r[cur][j];
+    if (ua) {
+      y = d.ybar[ab][j];
+      r = d.rbar[ab][j];
+      d.y[cur][j] = y;
+      d.r[cur][j] = r;
+      d.Bw[cur][j] = d.Bwbar[j];
+    }
+    d.yst[j] = y;
+    d.rst[j] = r;
+    d.ybar[ab][j] = y;
+    d.rbar[ab][j] = r;
+    if (j >= d.mE) {
+      T s = d.s[cur][j];
+      if (ua) {
+        s = d.sbar[ab][j];
+        d.s[cur][j] = s;
+      }
+      d.sst[j] = s;
+      d.sbar[ab][j] = s;
+    }
+  }
+}
+
+// ===========================================================================
+// Setup of one inner solve (a0): warm start, penalty + inner Ruiz scaling,
+// diagonal steps, cached products.
+// ===========================================================================
+
+// q_x = c - gamma^-1 z (Eq. inner-qp); bounds in T.
+template <typename T>
+__global__ void k_form_qx(Dev<T> d, const double *c, const double *z, double ginv) {
+  PDNQP_GRID_STRIDE(i, d.n) d.qx[i] = T(c[i] - z[i] * ginv);
+}
+
+// Eq. inner-warm-start: s = P_[l_c,u_c](A_I x + lambda / sigma), r_E = A_E x - b_E,
+// r_I = A_I x - s, and the cached B w = A x - s - r.
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_warm_rows(Dev<T> d) {
+  const int cur = d.st->cur;
+  const T *__restrict__ x = d.x[cur];
+  GroupIter<G> it;
+  for (long long base = it.first; base < d.m; base += it.step) {
+    const long long j = base + it.sub;
+    const bool valid = j < d.m;
+    const T ax = row_sum<G, T>(d.A.rp, d.A.ci, d.A.val, j, valid, it.lane_g, [&](int k, T a) { return a * x[k]; });
+    if (valid && it.lane_g == 0) {
+      T r, bw;
+      if (j >= d.mE) {
+        const T s = clampv<T>(T(double(ax) + d.lam[j] / d.sig[j]), d.ls[j], d.us[j]);
+        r = ax - s;
+        d.s[cur][j] = s;
+        bw = ax - s - r;
+      } else {
+        r = ax - d.h[j];
+        bw = ax - r;
+      }
+      d.r[cur][j] = r;
+      d.Bw[cur][j] = bw;
+    }
+  }
+}
+
+// Penalty scaling as the initial column scale of the r block: e_r = 1/sqrt(sigma).
+template <typename T>
+__global__ void k_iscale_init(Dev<T> d) {
+  PDNQP_GRID_STRIDE(i, d.n) d.ex[i] = T(1);
+  PDNQP_GRID_STRIDE(j, d.m) {
+    d.es[j] = T(1);
+    d.er[j] = T(1.0 / sqrt(d.sig[j]));
+    d.dy[j] = T(1);
+  }
+}
+
+// Inner Ruiz, l_inf norms of the x columns of [[H~, B~^T], [B~, 0]]:
+// max(max_k |e_k H_ki e_i|, max_j |d_j A_ji e_i|).
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_iruiz_cols(Dev<T> d, double *cnx) {
+  GroupIter<G> it;
+  for (long long base = it.first; base < d.n; base += it.step) {
+    const long long i = base + it.sub;
+    const bool valid = i < d.n;
+    const double ei = valid ? double(d.ex[i]) : 0.0;
+    const double a = row_max<G, double>(d.H.rp, d.H.ci, d.H.val, i, valid, it.lane_g,
+                                        [&](int k, T v) { return fabs(double(d.ex[k]) * double(v) * ei); });
+    const double b = row_max<G, double>(d.At.rp, d.At.ci, d.At.val, i, valid, it.lane_g,
+                                        [&](int k, T v) { return fabs(double(d.dy[k]) * double(v) * ei); });
+    if (valid && it.lane_g == 0) cnx[i] = fmax(a, b);
+  }
+}
+
+// Inner Ruiz, rows of B~ and the s / r columns: row j: max(max_k |d_j A_jk e_k|,
+// d_j e_s (I rows), d_j e_r); s column: d_j e_s; r column: max(e_r^2 sigma_j, d_j e_r).
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_iruiz_rows(Dev<T> d, double *rn, double *cns, double *cnr) {
+  GroupIter<G> it;
+  for (long long base = it.first; base < d.m; base += it.step) {
+    const long long j = base + it.sub;
+    const bool valid = j < d.m;
+    const double dj = valid ? double(d.dy[j]) : 0.0;
+    const double a = row_max<G, double>(d.A.rp, d.A.ci, d.A.val, j, valid, it.lane_g,
+                                        [&](int k, T v) { return fabs(dj * double(v) * double(d.ex[k])); });
+    if (valid && it.lane_g == 0) {
+      const double er = double(d.er[j]);
+      double rowv = fmax(a, dj * er);
+      if (j >= d.mE) {
+        const double es = double(d.es[j]);
+        rowv = fmax(rowv, dj * es);
+        cns[j] = dj * es;
+      }
+      rn[j] = rowv;
+      cnr[j] = fmax(er * er * d.sig[j], dj * er);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_iruiz_update(Dev<T> d, const double *cnx, const double *rn, const double *cns, const double *cnr) {
+  PDNQP_GRID_STRIDE(i, d.n) {
+    const double c = cnx[i];
+    if (c > 0.0) d.ex[i] = T(double(d.ex[i]) * (1.0 / sqrt(c)));
+  }
+  PDNQP_GRID_STRIDE(j, d.m) {
+    const double r = rn[j];
+    if (r > 0.0) d.dy[j] = T(double(d.dy[j]) * (1.0 / sqrt(r)));
+    const double cr = cnr[j];
+    if (cr > 0.0) d.er[j] = T(double(d.er[j]) * (1.0 / sqrt(cr)));
+    if (j >= d.mE) {
+      const double cs = cns[j];
+      if (cs > 0.0) d.es[j] = T(double(d.es[j]) * (1.0 / sqrt(cs)));
+    }
+  }
+}
+
+// Eq. diagonal-scales for the x columns (m_w) and the effective primal step
+// tau_eff / (kappa / omega) = e^2 * 0.99 / m_w (Eq. diagonal-steps).
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_mw_cols(Dev<T> d, double *mwx) {
+  GroupIter<G> it;
+  for (long long base = it.first; base < d.n; base += it.step) {
+    const long long i = base + it.sub;
+    const bool valid = i < d.n;
+    const double ei = valid ? double(d.ex[i]) : 0.0;
+    const double h1 = row_sum<G, double>(d.H.rp, d.H.ci, d.H.val, i, valid, it.lane_g,
+                                         [&](int k, T v) { return fabs(double(d.ex[k]) * double(v) * ei); });
+    const double b1 = row_sum<G, double>(d.At.rp, d.At.ci, d.At.val, i, valid, it.lane_g,
+                                         [&](int k, T v) { return fabs(double(d.dy[k]) * double(v) * ei); });
+    const double b2 = row_sum<G, double>(d.At.rp, d.At.ci, d.At.val, i, valid, it.lane_g, [&](int k, T v) {
+      const double bb = double(d.dy[k]) * double(v) * ei;
+      return d.sig[k] * bb * bb;
+    });
+    if (valid && it.lane_g == 0) {
+      const double mw = h1 + fmax(b1, sqrt(b2));
+      mwx[i] = mw;
+      d.taux[i] = T(ei * ei * (0.99 / mw));
+    }
+  }
+}
+
+// m_w of the s and r columns, their steps, and m_y with the dual step
+// eta_eff / (kappa omega) = d^2 * 0.99 / m_y.
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_my_rows(Dev<T> d, const double *mwx) {
+  GroupIter<G> it;
+  for (long long base = it.first; base < d.m; base += it.step) {
+    const long long j = base + it.sub;
+    const bool valid = j < d.m;
+    const double dj = valid ? double(d.dy[j]) : 0.0;
+    const double a = row_sum<G, double>(d.A.rp, d.A.ci, d.A.val, j, valid, it.lane_g, [&](int k, T v) {
+      const double bb = dj * double(v) * double(d.ex[k]);
+      return bb * bb / mwx[k];
+    });
+    if (valid && it.lane_g == 0) {
+      const double sg = d.sig[j];
+      const double er = double(d.er[j]);
+      const double br = dj * er;
+      const double mwr = er * er * sg + br;
+      d.taur[j] = T(er * er * (0.99 / mwr));
+      double my = a + br * br / mwr;
+      if (j >= d.mE) {
+        const double es = double(d.es[j]);
+        const double bs = dj * es;
+        const double mws = fmax(bs, sqrt(sg * bs * bs));
+        d.taus[j] = T(es * es * (0.99 / mws));
+        my += bs * bs / mws;
+      }
+      d.eta[j] = T(dj * dj * (0.99 / my));
+    }
+  }
+}
+
+// Cached products of the inner start: H x and A' y.
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_cache_cols(Dev<T> d) {
+  const int cur = d.st->cur;
+  const T *__restrict__ x = d.x[cur];
+  const T *__restrict__ y = d.y[cur];
+  GroupIter<G> it;
+  for (long long base = it.first; base < d.n; base += it.step) {
+    const long long i = base + it.sub;
+    const bool valid = i < d.n;
+    const T hx = row_sum<G, T>(d.H.rp, d.H.ci, d.H.val, i, valid, it.lane_g, [&](int k, T a) { return a * x[k]; });
+    const T aty = row_sum<G, T>(d.At.rp, d.At.ci, d.At.val, i, valid, it.lane_g, [&](int k, T a) { return a * y[k]; });
+    if (valid && it.lane_g == 0) {
+      d.Hx[cur][i] = hx;
+      d.Aty[cur][i] = aty;
+    }
+  }
+}
+
+// Epoch start and averages of the inner start (buffer 0).
+template <typename T>
+__global__ void k_inner_init(Dev<T> d) {
+  const int cur = d.st->cur;
+  PDNQP_GRID_STRIDE(i, d.n) {
+    d.xst[i] = d.x[cur][i];
+    d.xbar[0][i] = d.x[cur][i];
+    d.Hxbar[0][i] = d.Hx[cur][i];
+  }
+  PDNQP_GRID_STRIDE(j, d.m) {
+    d.yst[j] = d.y[cur][j];
+    d.rst[j] = d.r[cur][j];
+    d.ybar[0][j] = d.y[cur][j];
+    d.rbar[0][j] = d.r[cur][j];
+    if (j >= d.mE) {
+      d.sst[j] = d.s[cur][j];
+      d.sbar[0][j] = d.s[cur][j];
+    }
+  }
+}
+
+// Restart metric of the inner start (single block).
+__global__ void __launch_bounds__(kRedThreads) k_inner_begin(DevState *st, const double *part, int nb_r, int nb_c) {
+  double a[16], b[16];
+  final_reduce<16>(part + P_CK_R * kMaxBlocks, nb_r, CK_MAXMASK, a);
+  final_reduce<16>(part + P_CK_C * kMaxBlocks, nb_c, CK_MAXMASK, b);
+  if (threadIdx.x != 0) return;
+  const double om = st->omega;
+  st->k_restart = sqrt(om * (a[4] + b[4]) + (a[5] + b[5]) / om);
+  st->k_last = INFINITY;
+  st->status = ST_RUNNING;
+}
+
+}  // namespace
+}  // namespace pdq

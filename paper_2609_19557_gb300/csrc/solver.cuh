@@ -1,0 +1,81 @@
+// Host orchestration of the PDNQP solver on one GPU: setup (Sec. 3.1), the
+// outer proximal-ALM loop (Algorithm 3) on the host with its vector work in
+// kernels, and the inner rAPDHG solve (Algorithm 4) driven entirely by the
+// device: a CUDA graph of `chunk` trial slots is replayed, each slot being
+// [primal, rows, cols, decide, average, check-rows, check-cols, check-final,
+// check-apply]; every kernel reads the device-resident state and does nothing
+// once the inner solve has stopped, so the host only polls the status
+// between graph launches (Sec. 3.4, "GPU inner iterations").
+#pragma once
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/pdnqp.h"
+#include "common.cuh"
+
+namespace pdq {
+
+// Problem data after validation, classification (rows E first) and CSR
+// construction on the host.
+struct HostProblem {
+  int n = 0, m = 0, mE = 0;
+  std::vector<int> q_rp, q_ci, q_diag;
+  std::vector<double> q_v;
+  std::vector<int> a_rp, a_ci;
+  std::vector<double> a_v;
+  std::vector<int> at_rp, at_ci;
+  std::vector<double> at_v;
+  std::vector<double> c, lc, uc, lx, ux;  // lc/uc in internal row order; +-inf for absent bounds
+  std::vector<int> perm;                  // internal row -> original row
+};
+
+// Algorithm parameters: Table tab:parameters plus the readings of the rules
+// the paper leaves open.
+struct Params {
+  double time_limit = 1e30;
+  long long k_out = 2147483647LL, k_in = 40000;
+  double sigma_init = 20.0, theta_sigma = 0.25, delta_gamma = 1e-2;
+  double rho_in_min = 0.3, rho_in_max = 0.95, rho_z = 0.95;
+  int ruiz_outer = 8, ruiz_inner = 8, lanczos_steps = 64, k_chk = 64;
+  double beta_suff = 0.2, beta_nec = 0.8, beta_art = 0.36;
+  int rej_limit = 60;
+  double kappa_shrink = 0.5;
+  double delta_sigma = 2.0, sigma_max = 1e6, tol_floor = 0.1;
+  double gamma_override = 0.0;
+  int chunk = 32;
+  int g_rows = 0, g_cols = 0;  // lanes per CSR row (0 = from the mean row length)
+};
+
+struct Result {
+  int status = -1;
+  double rp = 0, rd = 0, sp = 1, sd = 1, rel_kkt = 0;
+  long long outer = 0, inner = 0, trials = 0, restarts = 0, passes = 0;
+  double seconds = 0, obj = 0;
+};
+
+class SolverBase {
+ public:
+  virtual ~SolverBase() {}
+  virtual int setup(const HostProblem &P, const Params &prm, std::string *err) = 0;
+  virtual int solve(double ea, double er, Params &prm, std::string *err) = 0;
+  virtual int get(double *x_int_orig, double *lam_int_orig, Result *r) = 0;
+  virtual int set_start(const double *x0, const double *lam0_int) = 0;
+  virtual int debug_inner(Params &prm, int nck, const int64_t *ck, double *snap, std::string *err) = 0;
+  virtual int replay(int which, int reps) = 0;
+  virtual double kernel_bytes(int which) const = 0;
+  virtual double gamma() const = 0;
+  virtual double lambda_min() const = 0;
+  virtual void set_gamma(double g) = 0;
+  virtual int64_t nnz_q() const = 0;
+};
+
+SolverBase *make_solver_f64(cudaStream_t s);
+SolverBase *make_solver_f32(cudaStream_t s);
+
+}  // namespace pdq

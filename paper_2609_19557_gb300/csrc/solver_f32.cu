@@ -1,0 +1,8 @@
+// FP32-bulk form of the solver: SpMVs and vector updates of the inner loop in
+// FP32 with FP32 accumulation; acceptance sums, check/restart/termination
+// reductions, multiplier and penalty updates and the setup in FP64.
+#include "solver_impl.cuh"
+
+namespace pdq {
+SolverBase *make_solver_f32(cudaStream_t s) { return new Solver<float>(s); }
+}  // namespace pdq

@@ -1,0 +1,848 @@
+// Templated implementation of SolverBase (T = double: plain FP64 form,
+// T = float: FP32-bulk form).  Included by exactly one .cu per T.
+#pragma once
+#include <algorithm>
+#include <cstdio>
+
+#include "kernels.cuh"
+#include "kernels_outer.cuh"
+#include "solver.cuh"
+
+namespace pdq {
+
+#define PDNQP_CK(expr)                                                            \
+  do {                                                                            \
+    cudaError_t _e = (expr);                                                      \
+    if (_e != cudaSuccess) {                                                      \
+      last_err_ = std::string(#expr) + ": " + cudaGetErrorString(_e);             \
+      return PDNQP_ERR_CUDA;                                                      \
+    }                                                                             \
+  } while (0)
+
+template <typename F>
+static void with_G(int g, F f) {
+  switch (g) {
+    case 1: f(std::integral_constant<int, 1>()); break;
+    case 2: f(std::integral_constant<int, 2>()); break;
+    case 4: f(std::integral_constant<int, 4>()); break;
+    case 8: f(std::integral_constant<int, 8>()); break;
+    case 16: f(std::integral_constant<int, 16>()); break;
+    default: f(std::integral_constant<int, 32>()); break;
+  }
+}
+
+static int pick_g(long long nnz, long long rows) {
+  const double mean = rows > 0 ? (double)nnz / (double)rows : 1.0;
+  int g = 2;
+  while (g < 32 && g < mean) g *= 2;
+  return g;
+}
+
+template <typename T>
+class Solver : public SolverBase {
+ public:
+  explicit Solver(cudaStream_t s) : s_(s) {
+    // Stream capture needs a non-default stream: make one when none is given.
+    if (!s_ && cudaStreamCreateWithFlags(&s_, cudaStreamNonBlocking) == cudaSuccess) own_stream_ = true;
+  }
+  ~Solver() override {
+    if (s_) cudaStreamSynchronize(s_);
+    if (gexec_) cudaGraphExecDestroy(gexec_);
+    for (void *p : allocs_) cudaFree(p);
+    if (hst_) cudaFreeHost(hst_);
+    if (own_stream_) cudaStreamDestroy(s_);
+  }
+
+  // ------------------------------------------------------------------ setup
+  int setup(const HostProblem &P, const Params &prm, std::string *err) override {
+    int rc = setup_impl(P, prm);
+    if (rc < 0 && err) *err = last_err_;
+    return rc;
+  }
+
+  double gamma() const override { return gamma_; }
+  double lambda_min() const override { return lam_min_; }
+  int64_t nnz_q() const override { return nnzH_; }
+  void set_gamma(double g) override { gamma_pending_ = g; }
+
+  int set_start(const double *x0, const double *lam0_int) override {
+    // Stored in original coordinates / internal row order; applied at the next solve.
+    if (x0) {
+      has_x0_ = true;
+      h_x0_.assign(x0, x0 + n_);
+    } else {
+      has_x0_ = false;
+    }
+    if (lam0_int && m_) {
+      has_l0_ = true;
+      h_l0_.assign(lam0_int, lam0_int + m_);
+    } else {
+      has_l0_ = false;
+    }
+    return 0;
+  }
+
+  int solve(double ea, double er, Params &prm, std::string *err) override {
+    int rc = solve_impl(ea, er, prm);
+    if (rc < 0 && err) *err = last_err_;
+    return rc;
+  }
+
+  int debug_inner(Params &prm, int nck, const int64_t *ck, double *snap, std::string *err) override {
+    int rc = debug_impl(prm, nck, ck, snap);
+    if (rc < 0 && err) *err = last_err_;
+    return rc;
+  }
+
+  int get(double *x_orig, double *lam_int_orig, Result *r) override {
+    if (r) *r = res_;
+    if (!solved_once_) return (x_orig || lam_int_orig) ? PDNQP_ERR_STATE : 0;
+    if (x_orig && n_) PDNQP_CK(cudaMemcpy(x_orig, xo_, sizeof(double) * n_, cudaMemcpyDeviceToHost));
+    if (lam_int_orig && m_) PDNQP_CK(cudaMemcpy(lam_int_orig, lo_, sizeof(double) * m_, cudaMemcpyDeviceToHost));
+    return 0;
+  }
+
+  // Replays one hot kernel (measurement hook); writes trial buffers only.
+  int replay(int which, int reps) override {
+    if (!ready_) return PDNQP_ERR_STATE;
+    // The kernels are gated on a running status: set it, then restore.
+    DevState saved;
+    PDNQP_CK(cudaMemcpyAsync(&saved, st_, sizeof(DevState), cudaMemcpyDeviceToHost, s_));
+    PDNQP_CK(cudaStreamSynchronize(s_));
+    DevState run = saved;
+    run.status = ST_RUNNING;
+    PDNQP_CK(cudaMemcpyAsync(st_, &run, sizeof(DevState), cudaMemcpyHostToDevice, s_));
+    for (int k = 0; k < reps; ++k) {
+      if (which == 0) launch_cols();
+      else if (which == 1) launch_rows();
+      else launch_primal();
+    }
+    PDNQP_CK(cudaMemcpyAsync(st_, &saved, sizeof(DevState), cudaMemcpyHostToDevice, s_));
+    PDNQP_CK(cudaStreamSynchronize(s_));
+    return 0;
+  }
+
+  // Compulsory DRAM bytes (each array touched once, int32 indices, value size
+  // sizeof(T)); gathers of x / y assumed L2-resident.
+  double kernel_bytes(int which) const override {
+    const double v = sizeof(T), n = n_, m = m_, mI = m_ - mE_;
+    const double mat_h = (v + 4) * nnzH_ + 4 * (n + 1), mat_a = (v + 4) * nnzA_ + 4 * (m + 1);
+    const double mat_at = (v + 4) * nnzA_ + 4 * (n + 1);
+    // k_cols: H, A^T; reads x_tr, x, Hx, Aty, taux; writes Hx_tr, Aty_tr; gathers x_tr (n) and y_tr (m).
+    const double cols = mat_h + mat_at + v * n * 7 + v * m;
+    // k_rows: A; reads y, r, rbar, lam(8), sig(8), taur, Bw, eta, h + s, sbar?, taus, ls, us (I); writes r, Bw, y (+ s).
+    const double rows = mat_a + v * n + m * (8 * v + 16) + mI * 5 * v;
+    // k_primal: reads qx, Hxbar, Hx, Aty, x, taux, lx, ux; writes x_tr.
+    const double primal = 9 * v * n;
+    // k_average: reads/writes xbar, Hxbar (read x, Hx), ybar, rbar (+ sbar), (read y, r, s).
+    const double avg = 6 * v * n + 6 * v * m + 3 * v * mI;
+    if (which == 0) return cols;
+    if (which == 1) return rows;
+    if (which == 2) return primal;
+    if (which == 3) return avg;
+    return cols + rows + primal + avg;
+  }
+
+ private:
+  // ------------------------------------------------------------- helpers
+  template <typename U>
+  int dalloc(U **p, size_t count) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(U));
+    if (e != cudaSuccess) {
+      last_err_ = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+      return PDNQP_ERR_OOM;
+    }
+    allocs_.push_back(q);
+    *p = (U *)q;
+    return 0;
+  }
+  template <typename U>
+  int upload(U **p, const std::vector<U> &h) {
+    int rc = dalloc(p, h.size());
+    if (rc) return rc;
+    if (!h.empty()) PDNQP_CK(cudaMemcpyAsync(*p, h.data(), sizeof(U) * h.size(), cudaMemcpyHostToDevice, s_));
+    return 0;
+  }
+#define PDNQP_TRY(x)          \
+  do {                        \
+    int _r = (x);             \
+    if (_r < 0) return _r;    \
+  } while (0)
+
+  int grid_n() const { return grid_for(n_, kBlock); }
+  int grid_m() const { return grid_for(m_, kBlock); }
+  int grid_nm() const { return grid_for(std::max(n_, m_), kBlock); }
+  int grid_rows_g(long long rows, int g) const { return grid_for(rows, kBlock / g); }
+
+  int reduce_to_host(int nq, int nb, unsigned mask, double *out) {
+    k_reduce_rows<<<1, kRedThreads, 0, s_>>>(part_, nq, nb, mask, dred_);
+    PDNQP_CK(cudaGetLastError());
+    PDNQP_CK(cudaMemcpyAsync(hred_.data(), dred_, sizeof(double) * nq, cudaMemcpyDeviceToHost, s_));
+    PDNQP_CK(cudaStreamSynchronize(s_));
+    for (int q = 0; q < nq; ++q) out[q] = hred_[q];
+    return 0;
+  }
+
+  // -------------------------------------------------------- setup_impl
+  int setup_impl(const HostProblem &P, const Params &prm) {
+    n_ = P.n;
+    m_ = P.m;
+    mE_ = P.mE;
+    nnzA_ = P.a_ci.size();
+    nnzH_ = P.q_ci.size();
+    PDNQP_TRY(dalloc(&st_, 1));
+    PDNQP_CK(cudaMallocHost(&hst_, sizeof(DevState)));
+    PDNQP_TRY(dalloc(&part_, (size_t)kMaxPartials * kMaxBlocks));
+    PDNQP_TRY(dalloc(&dred_, 128));
+    hred_.resize(128);
+    // FP64 matrices.
+    int *qrp, *qci, *qdiag, *arp, *aci, *atrp, *atci;
+    PDNQP_TRY(upload(&qrp, P.q_rp));
+    PDNQP_TRY(upload(&qci, P.q_ci));
+    PDNQP_TRY(upload(&qdiag, P.q_diag));
+    PDNQP_TRY(upload(&qv_, P.q_v));
+    PDNQP_TRY(upload(&arp, P.a_rp));
+    PDNQP_TRY(upload(&aci, P.a_ci));
+    PDNQP_TRY(upload(&av_, P.a_v));
+    PDNQP_TRY(upload(&atrp, P.at_rp));
+    PDNQP_TRY(upload(&atci, P.at_ci));
+    PDNQP_TRY(upload(&atv_, P.at_v));
+    qdiag_ = qdiag;
+    Hd_ = {n_, qrp, qci, qv_};
+    Ad_ = {m_, arp, aci, av_};
+    Atd_ = {n_, atrp, atci, atv_};
+    gA_ = prm.g_rows ? prm.g_rows : pick_g(nnzA_, m_);
+    gN_ = prm.g_cols ? prm.g_cols : pick_g(std::max(nnzH_, nnzA_), n_);
+    // FP64 vectors.
+    PDNQP_TRY(upload(&c_, P.c));
+    PDNQP_TRY(upload(&lxd_, P.lx));
+    PDNQP_TRY(upload(&uxd_, P.ux));
+    PDNQP_TRY(upload(&lcd_, P.lc));
+    PDNQP_TRY(upload(&ucd_, P.uc));
+    PDNQP_TRY(dalloc(&Dc_, m_));
+    PDNQP_TRY(dalloc(&Dx_, n_));
+    PDNQP_TRY(dalloc(&lam_, m_));
+    PDNQP_TRY(dalloc(&sig_, m_));
+    PDNQP_TRY(dalloc(&rprev_, m_));
+    PDNQP_TRY(dalloc(&rcur_, m_));
+    PDNQP_TRY(dalloc(&z_, n_));
+    PDNQP_TRY(dalloc(&xo_, n_));
+    PDNQP_TRY(dalloc(&lo_, m_));
+    PDNQP_TRY(dalloc(&scn_[0], n_));
+    PDNQP_TRY(dalloc(&scn_[1], n_));
+    PDNQP_TRY(dalloc(&scm_[0], m_));
+    PDNQP_TRY(dalloc(&scm_[1], m_));
+    PDNQP_TRY(dalloc(&scm_[2], m_));
+    PDNQP_TRY(dalloc(&dx0_, n_));
+    PDNQP_TRY(dalloc(&dl0_, m_));
+    // ---- outer Ruiz on [[Q, A^T], [A, 0]] (Eq. scaled-problem)
+    k_fill_d<<<grid_m(), kBlock, 0, s_>>>(Dc_, m_, 1.0);
+    k_fill_d<<<grid_n(), kBlock, 0, s_>>>(Dx_, n_, 1.0);
+    for (int sw = 0; sw < prm.ruiz_outer; ++sw) {
+      if (m_)
+        with_G(gA_, [&](auto GG) {
+          k_oruiz_rows<decltype(GG)::value><<<grid_rows_g(m_, gA_), kBlock, 0, s_>>>(Ad_, Dc_, Dx_, scm_[0]);
+        });
+      with_G(gN_, [&](auto GG) {
+        k_oruiz_cols<decltype(GG)::value><<<grid_rows_g(n_, gN_), kBlock, 0, s_>>>(Atd_, Hd_, Dc_, Dx_, scn_[0]);
+      });
+      if (m_) k_ruiz_apply<<<grid_m(), kBlock, 0, s_>>>(Dc_, scm_[0], m_);
+      k_ruiz_apply<<<grid_n(), kBlock, 0, s_>>>(Dx_, scn_[0], n_);
+    }
+    PDNQP_CK(cudaGetLastError());
+    if (m_) {
+      k_scale_csr<<<grid_m(), kBlock, 0, s_>>>(m_, arp, aci, av_, Dc_, Dx_, 1.0);
+      k_scale_csr<<<grid_n(), kBlock, 0, s_>>>(n_, atrp, atci, atv_, Dx_, Dc_, 1.0);
+    }
+    k_scale_csr<<<grid_n(), kBlock, 0, s_>>>(n_, qrp, qci, qv_, Dx_, Dx_, 1.0);
+    k_scale_vec<<<grid_n(), kBlock, 0, s_>>>(c_, Dx_, n_, 0, 1.0);
+    // objective scalar c_s = 1 / max(1, ||Dx Q Dx||_inf, ||Dx c||_inf)
+    double qn, cn;
+    {
+      int nb = grid_rows_g(n_, gN_);
+      with_G(gN_, [&](auto GG) { k_rowabs_max<decltype(GG)::value><<<nb, kBlock, 0, s_>>>(Hd_, part_); });
+      PDNQP_TRY(reduce_to_host(1, nb, 1u, &qn));
+      nb = grid_n();
+      k_absmax<<<nb, kBlock, 0, s_>>>(c_, n_, part_);
+      PDNQP_TRY(reduce_to_host(1, nb, 1u, &cn));
+    }
+    cs_ = prm.ruiz_outer >= 0 ? 1.0 / std::max(1.0, std::max(qn, cn)) : 1.0;
+    k_mul_scalar<<<grid_for(nnzH_, kBlock), kBlock, 0, s_>>>(qv_, nnzH_, cs_);
+    k_mul_scalar<<<grid_n(), kBlock, 0, s_>>>(c_, n_, cs_);
+    {
+      int nb = grid_rows_g(n_, gN_);
+      with_G(gN_, [&](auto GG) { k_rowabs_max<decltype(GG)::value><<<nb, kBlock, 0, s_>>>(Hd_, part_); });
+      PDNQP_TRY(reduce_to_host(1, nb, 1u, &qnorm_));
+    }
+    // bounds in scaled coordinates
+    k_scale_vec<<<grid_n(), kBlock, 0, s_>>>(lxd_, Dx_, n_, 1, 1.0);
+    k_scale_vec<<<grid_n(), kBlock, 0, s_>>>(uxd_, Dx_, n_, 1, 1.0);
+    if (m_) {
+      k_scale_vec<<<grid_m(), kBlock, 0, s_>>>(lcd_, Dc_, m_, 0, 1.0);
+      k_scale_vec<<<grid_m(), kBlock, 0, s_>>>(ucd_, Dc_, m_, 0, 1.0);
+    }
+    PDNQP_CK(cudaGetLastError());
+    // ---- gamma (Eq. R-choice): two Lanczos starts, the smaller estimate.
+    double l1, l2;
+    PDNQP_TRY(lanczos(prm.lanczos_steps, 1ULL, &l1));
+    PDNQP_TRY(lanczos(prm.lanczos_steps, 2ULL, &l2));
+    lam_min_ = std::min(l1, l2);
+    gamma_ = prm.gamma_override > 0 ? prm.gamma_override
+                                     : 1.0 / (std::max(0.0, -lam_min_) + prm.delta_gamma * std::max(1.0, qnorm_));
+    // H = Qbar + gamma^-1 I
+    k_add_diag<<<grid_n(), kBlock, 0, s_>>>(n_, qdiag_, qv_, 1.0 / gamma_);
+    PDNQP_CK(cudaGetLastError());
+    // ---- T-typed copies and inner vectors
+    PDNQP_TRY(alloc_T());
+    PDNQP_CK(cudaStreamSynchronize(s_));
+    ready_ = true;
+    return 0;
+  }
+
+  int lanczos(int steps, unsigned long long seed, double *out) {
+    const long long n = n_;
+    if (n == 0) {
+      *out = 0.0;
+      return 0;
+    }
+    const int k = (int)std::min<long long>(std::min(steps, 79), n);  // part_lz() holds 80 rows
+    if (!V_) PDNQP_TRY(dalloc(&V_, (size_t)(k + 1) * n));
+    if (!hdev_) PDNQP_TRY(dalloc(&hdev_, 256));
+    double *w = scn_[1];
+    std::vector<double> al(k + 1, 0.0), be(k + 1, 0.0);
+    // Hd currently holds the scaled Q (gamma not yet added).
+    k_start_vector<<<grid_n(), kBlock, 0, s_>>>(V_, n, seed);
+    double nrm;
+    PDNQP_TRY(dot(V_, V_, &nrm));
+    k_scale_into<<<grid_n(), kBlock, 0, s_>>>(V_, V_, 1.0 / std::sqrt(nrm), n);
+    int used = 0;
+    const int nbd = grid_n();
+    for (int j = 0; j < k; ++j) {
+      double *vj = V_ + (long long)j * n;
+      with_G(gN_, [&](auto GG) {
+        k_spmv<decltype(GG)::value><<<grid_rows_g(n, gN_), kBlock, 0, s_>>>(Hd_, vj, w);
+      });
+      PDNQP_TRY(dot(w, vj, &al[j]));
+      used = j + 1;
+      k_lanczos_axpy<<<grid_n(), kBlock, 0, s_>>>(w, vj, j > 0 ? V_ + (long long)(j - 1) * n : nullptr, al[j],
+                                                   j > 0 ? be[j - 1] : 0.0, n);
+      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+        dim3 grid(nbd, j + 1);
+        k_multidot<<<grid, kBlock, 0, s_>>>(V_, n, w, part_lz());
+        k_reduce_rows<<<1, kRedThreads, 0, s_>>>(part_lz(), j + 1, nbd, 0u, hdev_);
+        k_multiaxpy<<<grid_n(), kBlock, 0, s_>>>(V_, n, hdev_, j + 1, w);
+      }
+      double b2;
+      PDNQP_TRY(dot(w, w, &b2));
+      const double b = std::sqrt(b2);
+      be[j] = b;
+      if (j == k - 1) break;
+      if (b <= 1e-12 * (std::fabs(al[j]) + (j > 0 ? be[j - 1] : 0.0) + 1e-300)) break;
+      k_scale_into<<<grid_n(), kBlock, 0, s_>>>(V_ + (long long)(j + 1) * n, w, 1.0 / b, n);
+    }
+    PDNQP_CK(cudaGetLastError());
+    *out = tridiag_min(al, be, used);
+    return 0;
+  }
+
+  // Smallest eigenvalue of the Lanczos tridiagonal by Sturm-count bisection.
+  static double tridiag_min(const std::vector<double> &a, const std::vector<double> &b, int k) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int i = 0; i < k; ++i) {
+      const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i < k - 1 ? std::fabs(b[i]) : 0.0);
+      lo = std::min(lo, a[i] - r);
+      hi = std::max(hi, a[i] + r);
+    }
+    auto below = [&](double x) {
+      int cnt = 0;
+      double dd = 1.0;
+      for (int i = 0; i < k; ++i) {
+        dd = (a[i] - x) - (i > 0 ? b[i - 1] * b[i - 1] / dd : 0.0);
+        if (dd == 0.0) dd = -1e-300;
+        if (dd < 0.0) ++cnt;
+      }
+      return cnt;
+    };
+    for (int it = 0; it < 400; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (below(mid) >= 1) hi = mid;
+      else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+  }
+
+  double *part_lz() { return lzpart_ ? lzpart_ : (dalloc(&lzpart_, (size_t)80 * kMaxBlocks), lzpart_); }
+
+  int dot(const double *a, const double *b, double *out) {
+    const int nb = grid_n();
+    k_dot<<<nb, kBlock, 0, s_>>>(a, b, n_, part_);
+    return reduce_to_host(1, nb, 0u, out);
+  }
+
+  int alloc_T() {
+    Dev<T> &d = d_;
+    d.n = n_;
+    d.m = m_;
+    d.mE = mE_;
+    if (std::is_same<T, double>::value) {
+      d.H = {Hd_.nrows, Hd_.rp, Hd_.ci, (const T *)Hd_.val};
+      d.A = {Ad_.nrows, Ad_.rp, Ad_.ci, (const T *)Ad_.val};
+      d.At = {Atd_.nrows, Atd_.rp, Atd_.ci, (const T *)Atd_.val};
+    } else {
+      T *hv, *av, *atv;
+      PDNQP_TRY(dalloc(&hv, nnzH_));
+      PDNQP_TRY(dalloc(&av, nnzA_));
+      PDNQP_TRY(dalloc(&atv, nnzA_));
+      k_to_T<T><<<grid_for(nnzH_, kBlock), kBlock, 0, s_>>>(hv, qv_, nnzH_);
+      if (nnzA_) {
+        k_to_T<T><<<grid_for(nnzA_, kBlock), kBlock, 0, s_>>>(av, av_, nnzA_);
+        k_to_T<T><<<grid_for(nnzA_, kBlock), kBlock, 0, s_>>>(atv, atv_, nnzA_);
+      }
+      d.H = {Hd_.nrows, Hd_.rp, Hd_.ci, hv};
+      d.A = {Ad_.nrows, Ad_.rp, Ad_.ci, av};
+      d.At = {Atd_.nrows, Atd_.rp, Atd_.ci, atv};
+    }
+    for (int b = 0; b < 2; ++b) {
+      PDNQP_TRY(dalloc(&d.x[b], n_));
+      PDNQP_TRY(dalloc(&d.Hx[b], n_));
+      PDNQP_TRY(dalloc(&d.Aty[b], n_));
+      PDNQP_TRY(dalloc(&d.xbar[b], n_));
+      PDNQP_TRY(dalloc(&d.Hxbar[b], n_));
+      PDNQP_TRY(dalloc(&d.y[b], m_));
+      PDNQP_TRY(dalloc(&d.s[b], m_));
+      PDNQP_TRY(dalloc(&d.r[b], m_));
+      PDNQP_TRY(dalloc(&d.Bw[b], m_));
+      PDNQP_TRY(dalloc(&d.ybar[b], m_));
+      PDNQP_TRY(dalloc(&d.sbar[b], m_));
+      PDNQP_TRY(dalloc(&d.rbar[b], m_));
+      PDNQP_CK(cudaMemsetAsync(d.s[b], 0, sizeof(T) * std::max(m_, 1), s_));
+      PDNQP_CK(cudaMemsetAsync(d.sbar[b], 0, sizeof(T) * std::max(m_, 1), s_));
+    }
+    T **nv[] = {&d.qx, &d.lx, &d.ux, &d.taux, &d.ex, &d.xst, &d.Atybar};
+    for (T **p : nv) PDNQP_TRY(dalloc(p, n_));
+    T **mv[] = {&d.eta, &d.taus, &d.taur, &d.es, &d.er, &d.dy, &d.h, &d.ls, &d.us, &d.yst, &d.sst, &d.rst, &d.Bwbar};
+    for (T **p : mv) {
+      PDNQP_TRY(dalloc(p, m_));
+      PDNQP_CK(cudaMemsetAsync(*p, 0, sizeof(T) * std::max(m_, 1), s_));
+    }
+    k_to_T<T><<<grid_n(), kBlock, 0, s_>>>(d.lx, lxd_, n_);
+    k_to_T<T><<<grid_n(), kBlock, 0, s_>>>(d.ux, uxd_, n_);
+    if (m_) {
+      k_to_T<T><<<grid_m(), kBlock, 0, s_>>>(d.ls, lcd_, m_);
+      k_to_T<T><<<grid_m(), kBlock, 0, s_>>>(d.us, ucd_, m_);
+      k_form_h<T><<<grid_m(), kBlock, 0, s_>>>(d.h, lcd_, m_, mE_);
+    }
+    d.lam = lam_;
+    d.sig = sig_;
+    d.part = part_;
+    d.st = st_;
+    PDNQP_CK(cudaGetLastError());
+    return 0;
+  }
+
+  // ------------------------------------------------------- launchers
+  int nb_rows() const { return grid_rows_g(std::max(m_, 1), gA_); }
+  int nb_cols() const { return grid_rows_g(n_, gN_); }
+  void launch_primal() { k_primal<T><<<grid_n(), kBlock, 0, s_>>>(d_); }
+  void launch_rows() {
+    with_G(gA_, [&](auto GG) { k_rows<T, decltype(GG)::value><<<nb_rows(), kBlock, 0, s_>>>(d_); });
+  }
+  void launch_cols() {
+    with_G(gN_, [&](auto GG) { k_cols<T, decltype(GG)::value><<<nb_cols(), kBlock, 0, s_>>>(d_); });
+  }
+  void launch_slot() {
+    launch_primal();
+    launch_rows();
+    launch_cols();
+    k_decide<<<1, kRedThreads, 0, s_>>>(st_, part_, nb_rows(), nb_cols());
+    k_average<T><<<grid_nm(), kBlock, 0, s_>>>(d_);
+    launch_check(0);
+    k_check_final<<<1, kRedThreads, 0, s_>>>(st_, part_, nb_rows(), nb_cols());
+    k_check_apply<T><<<grid_nm(), kBlock, 0, s_>>>(d_);
+  }
+  void launch_check(int mode) {
+    with_G(gA_, [&](auto GG) { k_check_rows<T, decltype(GG)::value><<<nb_rows(), kBlock, 0, s_>>>(d_, mode); });
+    with_G(gN_, [&](auto GG) { k_check_cols<T, decltype(GG)::value><<<nb_cols(), kBlock, 0, s_>>>(d_, mode); });
+  }
+
+  int build_graph(int chunk) {
+    if (gexec_ && chunk == graph_chunk_) return 0;
+    if (gexec_) {
+      cudaGraphExecDestroy(gexec_);
+      gexec_ = nullptr;
+    }
+    cudaGraph_t g;
+    PDNQP_CK(cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < chunk; ++k) launch_slot();
+    PDNQP_CK(cudaStreamEndCapture(s_, &g));
+    cudaError_t e = cudaGraphInstantiate(&gexec_, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      last_err_ = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+      return PDNQP_ERR_CUDA;
+    }
+    graph_chunk_ = chunk;
+    return 0;
+  }
+
+  // ----------------------------------------------------- solve state
+  // Initial point, multipliers, penalties (Sec. 3.2.1 and the QPALM rule).
+  int start_point(const Params &prm) {
+    DevState S;
+    memset(&S, 0, sizeof(S));
+    S.status = ST_IDLE;
+    S.cur = 0;
+    PDNQP_CK(cudaMemcpyAsync(st_, &S, sizeof(S), cudaMemcpyHostToDevice, s_));
+    if (has_x0_) PDNQP_CK(cudaMemcpyAsync(dx0_, h_x0_.data(), sizeof(double) * n_, cudaMemcpyHostToDevice, s_));
+    if (has_l0_) PDNQP_CK(cudaMemcpyAsync(dl0_, h_l0_.data(), sizeof(double) * m_, cudaMemcpyHostToDevice, s_));
+    k_init_x<T><<<grid_n(), kBlock, 0, s_>>>(d_, has_x0_ ? dx0_ : nullptr, Dx_, lxd_, uxd_, z_);
+    if (m_) k_init_lambda<T><<<grid_m(), kBlock, 0, s_>>>(d_, lam_, has_l0_ ? dl0_ : nullptr, Dc_, cs_);
+    // f(x0) and the constraint violation for sigma0
+    double ob[2];
+    {
+      const int nb = nb_cols();
+      with_G(gN_, [&](auto GG) {
+        k_objective<T, decltype(GG)::value><<<nb, kBlock, 0, s_>>>(d_, Hd_, c_, 1.0 / gamma_);
+      });
+      PDNQP_TRY(reduce_to_host(2, nb, 0u, ob));
+    }
+    double dist2 = 0.0;
+    if (m_) {
+      const int nb = nb_rows();
+      with_G(gA_, [&](auto GG) {
+        k_init_rows<T, decltype(GG)::value><<<nb, kBlock, 0, s_>>>(d_, Ad_, lcd_, ucd_, lam_, sig_, rprev_, 0);
+      });
+      PDNQP_TRY(reduce_to_host(1, nb, 0u, &dist2));
+    }
+    const double f0 = 0.5 * ob[0] + ob[1];
+    double s0 = prm.sigma_init * std::max(1.0, std::fabs(f0)) / std::max(1.0, 0.5 * dist2);
+    s0 = std::min(1e4, std::max(1e-4, s0));
+    sigma0_ = s0;
+    if (m_) {
+      k_fill_d<<<grid_m(), kBlock, 0, s_>>>(sig_, m_, s0);
+      with_G(gA_, [&](auto GG) {
+        k_init_rows<T, decltype(GG)::value><<<nb_rows(), kBlock, 0, s_>>>(d_, Ad_, lcd_, ucd_, lam_, sig_, rprev_, 1);
+      });
+    }
+    PDNQP_CK(cudaGetLastError());
+    omega_ = 1.0;
+    trials_ = accepted_ = restarts_ = 0;
+    return 0;
+  }
+
+  // a0: setup of one inner solve (Algorithm 4 lines "warm start" and "inner scaling").
+  int inner_setup(const Params &prm, double dta, double dtr, long long k_in, long long pause_at, int ignore) {
+    const double ginv = 1.0 / gamma_;
+    k_form_qx<T><<<grid_n(), kBlock, 0, s_>>>(d_, c_, z_, ginv);
+    if (m_) with_G(gA_, [&](auto GG) { k_warm_rows<T, decltype(GG)::value><<<nb_rows(), kBlock, 0, s_>>>(d_); });
+    k_iscale_init<T><<<grid_nm(), kBlock, 0, s_>>>(d_);
+    for (int sw = 0; sw < prm.ruiz_inner; ++sw) {
+      with_G(gN_, [&](auto GG) {
+        k_iruiz_cols<T, decltype(GG)::value><<<nb_cols(), kBlock, 0, s_>>>(d_, scn_[0]);
+      });
+      if (m_)
+        with_G(gA_, [&](auto GG) {
+          k_iruiz_rows<T, decltype(GG)::value><<<nb_rows(), kBlock, 0, s_>>>(d_, scm_[0], scm_[1], scm_[2]);
+        });
+      k_iruiz_update<T><<<grid_nm(), kBlock, 0, s_>>>(d_, scn_[0], scm_[0], scm_[1], scm_[2]);
+    }
+    with_G(gN_, [&](auto GG) { k_mw_cols<T, decltype(GG)::value><<<nb_cols(), kBlock, 0, s_>>>(d_, scn_[0]); });
+    if (m_) with_G(gA_, [&](auto GG) { k_my_rows<T, decltype(GG)::value><<<nb_rows(), kBlock, 0, s_>>>(d_, scn_[0]); });
+    with_G(gN_, [&](auto GG) { k_cache_cols<T, decltype(GG)::value><<<nb_cols(), kBlock, 0, s_>>>(d_); });
+    k_inner_init<T><<<grid_nm(), kBlock, 0, s_>>>(d_);
+    // Device state of this solve.
+    DevState S;
+    PDNQP_CK(cudaMemcpyAsync(&S, st_, sizeof(S), cudaMemcpyDeviceToHost, s_));
+    PDNQP_CK(cudaStreamSynchronize(s_));
+    S.status = ST_IDLE;
+    S.accepted = 0;
+    S.acur = 0;
+    S.check_due = 0;
+    S.restart_flag = 0;
+    S.ret_avg = 0;
+    S.ignore_conv = ignore;
+    S.t = 0;
+    S.t_total = 0;
+    S.trials = trials_;
+    S.accepted_all = accepted_;
+    S.restarts = restarts_;
+    S.rej = 0;
+    S.k_in = k_in;
+    S.pause_at = pause_at;
+    S.k_chk = prm.k_chk;
+    S.rej_limit = prm.rej_limit;
+    S.kappa = 1.0;
+    S.omega = omega_;
+    S.alpha_acc = 1.0;
+    S.dta = dta;
+    S.dtr = dtr;
+    S.shrink = prm.kappa_shrink;
+    S.beta_suff = prm.beta_suff;
+    S.beta_nec = prm.beta_nec;
+    S.beta_art = prm.beta_art;
+    PDNQP_CK(cudaMemcpyAsync(st_, &S, sizeof(S), cudaMemcpyHostToDevice, s_));
+    launch_check(1);
+    k_inner_begin<<<1, kRedThreads, 0, s_>>>(st_, part_, nb_rows(), nb_cols());
+    PDNQP_CK(cudaGetLastError());
+    return 0;
+  }
+
+  int read_state(DevState *S) {
+    PDNQP_CK(cudaMemcpyAsync(hst_, st_, sizeof(DevState), cudaMemcpyDeviceToHost, s_));
+    PDNQP_CK(cudaStreamSynchronize(s_));
+    *S = *hst_;
+    return 0;
+  }
+
+  // Runs graph chunks until the device status leaves RUNNING.
+  int run_until_stop(const Params &prm, DevState *S, double t0) {
+    PDNQP_TRY(build_graph(prm.chunk));
+    for (;;) {
+      PDNQP_CK(cudaGraphLaunch(gexec_, s_));
+      PDNQP_TRY(read_state(S));
+      if (S->status != ST_RUNNING) return 0;
+      if (seconds_since(t0) > prm.time_limit) return 1;
+    }
+  }
+
+  static double now() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+  }
+  static double seconds_since(double t0) { return now() - t0; }
+
+  int finish_inner(const DevState &S) {
+    trials_ = S.trials;
+    accepted_ = S.accepted_all;
+    restarts_ = S.restarts;
+    omega_ = S.omega;
+    const int cur = S.cur;
+    if (cur != 0) {
+      // Keep the outer x / inner y in buffer 0 so the next solve starts there.
+      PDNQP_CK(cudaMemcpyAsync(d_.x[0], d_.x[1], sizeof(T) * n_, cudaMemcpyDeviceToDevice, s_));
+      if (m_) PDNQP_CK(cudaMemcpyAsync(d_.y[0], d_.y[1], sizeof(T) * m_, cudaMemcpyDeviceToDevice, s_));
+    }
+    if (S.status == ST_CONVERGED && S.ret_avg) {
+      const int ab = S.acur ^ S.accepted;
+      PDNQP_CK(cudaMemcpyAsync(d_.x[0], d_.xbar[ab], sizeof(T) * n_, cudaMemcpyDeviceToDevice, s_));
+      if (m_) PDNQP_CK(cudaMemcpyAsync(d_.y[0], d_.ybar[ab], sizeof(T) * m_, cudaMemcpyDeviceToDevice, s_));
+    }
+    DevState Z = S;
+    Z.cur = 0;
+    Z.status = ST_IDLE;
+    PDNQP_CK(cudaMemcpyAsync(st_, &Z, sizeof(Z), cudaMemcpyHostToDevice, s_));
+    return 0;
+  }
+
+  // Outer residuals; update = 1 also applies the multiplier update first.
+  int outer_residuals(int update, double *q) {
+    const double ginv = 1.0 / gamma_;
+    double a[12] = {0}, b[12] = {0};
+    if (m_) {
+      const int nb = nb_rows();
+      with_G(gA_, [&](auto GG) {
+        k_outer_rows<T, decltype(GG)::value><<<nb, kBlock, 0, s_>>>(d_, Ad_, lcd_, ucd_, Dc_, lam_, sig_, rcur_,
+                                                                     update);
+      });
+      PDNQP_TRY(reduce_to_host(12, nb, OUT_MAXMASK, a));
+    }
+    const int nb = nb_cols();
+    with_G(gN_, [&](auto GG) {
+      k_outer_cols<T, decltype(GG)::value><<<nb, kBlock, 0, s_>>>(d_, Hd_, Atd_, c_, lxd_, uxd_, Dx_, lam_, z_,
+                                                                   ginv, cs_);
+    });
+    k_reduce_rows<<<1, kRedThreads, 0, s_>>>(part_ + 12 * kMaxBlocks, 12, nb, OUT_MAXMASK, dred_);
+    PDNQP_CK(cudaMemcpyAsync(hred_.data(), dred_, sizeof(double) * 12, cudaMemcpyDeviceToHost, s_));
+    PDNQP_CK(cudaStreamSynchronize(s_));
+    for (int k = 0; k < 12; ++k) b[k] = hred_[k];
+    for (int k = 0; k < 12; ++k) q[k] = ((OUT_MAXMASK >> k) & 1u) ? std::max(a[k], b[k]) : a[k] + b[k];
+    return 0;
+  }
+
+  int solve_impl(double ea, double er, Params &prm) {
+    if (!ready_) return PDNQP_ERR_STATE;
+    const double t0 = now();
+    if (gamma_pending_ > 0) {
+      PDNQP_TRY(regamma(gamma_pending_));
+      gamma_pending_ = 0;
+    }
+    PDNQP_TRY(start_point(prm));
+    double dta = 1.0, dtr = 1.0, eak = 1.0, erk = 1.0;
+    int status = PDNQP_ITER_LIMIT;
+    long long k;
+    double q[12];
+    for (k = 0; k < prm.k_out; ++k) {
+      if (seconds_since(t0) > prm.time_limit) {
+        status = PDNQP_TIME_LIMIT;
+        break;
+      }
+      PDNQP_TRY(inner_setup(prm, dta, dtr, prm.k_in, -1, 0));
+      DevState S;
+      int tl = 0;
+      PDNQP_TRY(tl = run_until_stop(prm, &S, t0));
+      if (tl == 1) {
+        // time limit inside the inner solve: stop the device loop
+        PDNQP_TRY(read_state(&S));
+        PDNQP_TRY(finish_inner(S));
+        status = PDNQP_TIME_LIMIT;
+        ++k;
+        break;
+      }
+      PDNQP_TRY(finish_inner(S));
+      if (S.status == ST_NUMERICAL_ERROR) {
+        status = PDNQP_NUMERICAL_ERROR;
+        ++k;
+        break;
+      }
+      if (S.status == ST_ITER_LIMIT) continue;
+      // Multiplier update + outer residuals (Eqs. practical-multiplier-update, outer-residuals).
+      PDNQP_TRY(outer_residuals(1, q));
+      const double rps = q[0], sps = std::max(1.0, q[1]), rpu = q[2], spu = std::max(1.0, q[3]), rn = q[4];
+      const double rds = q[5], rdu = q[7], sdu = std::max(1.0, q[8]), dxz = q[9];
+      (void)rps;
+      if (rpu <= ea + er * spu && rdu <= ea + er * sdu) {
+        status = PDNQP_SOLVED;
+        ++k;
+        break;
+      }
+      // Eq. penalty-trigger-eq.
+      if (m_)
+        k_sigma_update<<<grid_m(), kBlock, 0, s_>>>(m_, mE_, sig_, lam_, rcur_, rprev_, prm.theta_sigma,
+                                                    ea + er * sps, rn, prm.delta_sigma, prm.sigma_max);
+      // Eq. inner-tolerance-factor.
+      const double ratio = rds > 0.0 ? std::min(1.0, (dxz / gamma_) / rds) : 1.0;
+      const double rho = prm.rho_in_max - (prm.rho_in_max - prm.rho_in_min) * ratio;
+      dta = std::max(dta * rho, prm.tol_floor * ea);
+      dtr = std::max(dtr * rho, prm.tol_floor * er);
+      // Eq. center-update / center-tolerance-update.
+      if (rps <= eak + erk * sps) {
+        k_copy_to_double<T><<<grid_n(), kBlock, 0, s_>>>(z_, d_.x[0], n_);
+        eak *= prm.rho_z;
+        erk *= prm.rho_z;
+      }
+      PDNQP_CK(cudaGetLastError());
+    }
+    // Result in the original coordinates.
+    PDNQP_TRY(outer_residuals(0, q));
+    k_unscale<T><<<grid_nm(), kBlock, 0, s_>>>(d_.x[0], Dx_, n_, lam_, Dc_, m_, cs_, xo_, lo_);
+    PDNQP_CK(cudaGetLastError());
+    PDNQP_CK(cudaStreamSynchronize(s_));
+    res_.status = status;
+    res_.rp = q[2];
+    res_.sp = std::max(1.0, q[3]);
+    res_.rd = q[7];
+    res_.sd = std::max(1.0, q[8]);
+    res_.rel_kkt = std::max(res_.rp / (1.0 + res_.sp), res_.rd / (1.0 + res_.sd));
+    res_.obj = (0.5 * q[10] + q[11]) / cs_;
+    res_.outer = k;
+    res_.inner = accepted_;
+    res_.trials = trials_;
+    res_.restarts = restarts_;
+    res_.passes = 3 * trials_ + 2 * (accepted_ / std::max(1, prm.k_chk));
+    res_.seconds = seconds_since(t0);
+    solved_once_ = true;
+    return status;
+  }
+
+  int regamma(double g) {
+    // Replace gamma: H = Qbar + g^-1 I (undo the previous shift).
+    k_add_diag<<<grid_n(), kBlock, 0, s_>>>(n_, qdiag_, qv_, 1.0 / g - 1.0 / gamma_);
+    gamma_ = g;
+    if (!std::is_same<T, double>::value)
+      k_to_T<T><<<grid_for(nnzH_, kBlock), kBlock, 0, s_>>>((T *)d_.H.val, qv_, nnzH_);
+    PDNQP_CK(cudaGetLastError());
+    return 0;
+  }
+
+  int snapshot(const DevState &S, double *o) {
+    const long long n = n_, m = m_, mI = m_ - mE_, dw = n + mI + m;
+    const int cur = S.cur, ab = S.acur ^ S.accepted;
+    std::vector<T> tx(std::max(n, m));
+    auto put = [&](const T *src, long long cnt, long long off, long long src_off) -> int {
+      if (cnt == 0) return 0;
+      PDNQP_CK(cudaMemcpyAsync(tx.data(), src + src_off, sizeof(T) * cnt, cudaMemcpyDeviceToHost, s_));
+      PDNQP_CK(cudaStreamSynchronize(s_));
+      for (long long i = 0; i < cnt; ++i) o[off + i] = double(tx[i]);
+      return 0;
+    };
+    // w = (x, s_I, r_E, r_I); s rows mE..m-1 hold s_I, r rows are E then I.
+    PDNQP_TRY(put(d_.x[cur], n, 0, 0));
+    PDNQP_TRY(put(d_.s[cur], mI, n, mE_));
+    PDNQP_TRY(put(d_.r[cur], m, n + mI, 0));
+    PDNQP_TRY(put(d_.y[cur], m, dw, 0));
+    PDNQP_TRY(put(d_.xbar[ab], n, dw + m, 0));
+    PDNQP_TRY(put(d_.sbar[ab], mI, dw + m + n, mE_));
+    PDNQP_TRY(put(d_.rbar[ab], m, dw + m + n + mI, 0));
+    PDNQP_TRY(put(d_.ybar[ab], m, 2 * dw + m, 0));
+    double *sc = o + 2 * (dw + m);
+    sc[0] = S.omega;
+    sc[1] = S.kappa;
+    sc[2] = (double)S.t;
+    sc[3] = (double)S.t_total;
+    sc[4] = (double)S.trials;
+    sc[5] = (double)S.restarts;
+    sc[6] = S.k_restart;
+    sc[7] = S.k_last;
+    return 0;
+  }
+
+  int debug_impl(Params &prm, int nck, const int64_t *ck, double *snap) {
+    if (!ready_) return PDNQP_ERR_STATE;
+    if (gamma_pending_ > 0) {
+      PDNQP_TRY(regamma(gamma_pending_));
+      gamma_pending_ = 0;
+    }
+    PDNQP_TRY(start_point(prm));
+    const long long len = 2 * ((long long)n_ + (m_ - mE_) + m_ + m_) + 8;
+    int got = 0;
+    PDNQP_TRY(inner_setup(prm, 1.0, 1.0, (long long)4e18, nck > 0 ? ck[0] : -1, 1));
+    const double t0 = now();
+    while (got < nck) {
+      DevState S;
+      int tl = 0;
+      PDNQP_TRY(tl = run_until_stop(prm, &S, t0));
+      if (tl == 1 || S.status != ST_PAUSED) break;
+      PDNQP_TRY(snapshot(S, snap + (long long)got * len));
+      ++got;
+      S.status = ST_RUNNING;
+      S.pause_at = got < nck ? ck[got] : -1;
+      PDNQP_CK(cudaMemcpyAsync(st_, &S, sizeof(S), cudaMemcpyHostToDevice, s_));
+    }
+    DevState S;
+    PDNQP_TRY(read_state(&S));
+    (void)S;
+    return got;
+  }
+
+ public:
+  // members
+  cudaStream_t s_;
+  std::string last_err_;
+  std::vector<void *> allocs_;
+  int n_ = 0, m_ = 0, mE_ = 0;
+  long long nnzA_ = 0, nnzH_ = 0;
+  int gA_ = 8, gN_ = 8;
+  Mat<double> Hd_{}, Ad_{}, Atd_{};
+  double *qv_ = nullptr, *av_ = nullptr, *atv_ = nullptr;
+  int *qdiag_ = nullptr;
+  double *c_ = nullptr, *lxd_ = nullptr, *uxd_ = nullptr, *lcd_ = nullptr, *ucd_ = nullptr;
+  double *Dc_ = nullptr, *Dx_ = nullptr, *lam_ = nullptr, *sig_ = nullptr, *rprev_ = nullptr, *rcur_ = nullptr;
+  double *z_ = nullptr, *xo_ = nullptr, *lo_ = nullptr, *dx0_ = nullptr, *dl0_ = nullptr;
+  double *scn_[2] = {nullptr, nullptr}, *scm_[3] = {nullptr, nullptr, nullptr};
+  double *V_ = nullptr, *hdev_ = nullptr, *lzpart_ = nullptr;
+  double *part_ = nullptr, *dred_ = nullptr;
+  std::vector<double> hred_;
+  DevState *st_ = nullptr, *hst_ = nullptr;
+  Dev<T> d_{};
+  cudaGraphExec_t gexec_ = nullptr;
+  int graph_chunk_ = 0;
+  double cs_ = 1.0, qnorm_ = 0.0, gamma_ = 1.0, lam_min_ = 0.0, sigma0_ = 1.0, omega_ = 1.0;
+  double gamma_pending_ = 0.0;
+  long long trials_ = 0, accepted_ = 0, restarts_ = 0;
+  bool ready_ = false, solved_once_ = false, has_x0_ = false, has_l0_ = false, own_stream_ = false;
+  std::vector<double> h_x0_, h_l0_;
+  Result res_;
+};
+
+}  // namespace pdq

@@ -1,0 +1,217 @@
+"""Thin ctypes binding of libpdnqp.so (include/pdnqp.h), same names as the C ABI.
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  There is no fallback: if the shared library is missing or no
+GPU is usable, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpdnqp.so")
+
+PDNQP_SOLVED, PDNQP_PRIMAL_INFEASIBLE, PDNQP_DUAL_INFEASIBLE = 0, 1, 2
+PDNQP_ITER_LIMIT, PDNQP_TIME_LIMIT, PDNQP_NUMERICAL_ERROR = 3, 4, 5
+PDNQP_FP64, PDNQP_FP32_BULK = 64, 32
+STATUS_NAMES = {0: "SOLVED", 1: "PRIMAL_INFEASIBLE", 2: "DUAL_INFEASIBLE", 3: "ITER_LIMIT", 4: "TIME_LIMIT",
+                5: "NUMERICAL_ERROR"}
+SNAP_SCALARS = 8
+
+# Every function declared in include/pdnqp.h.
+EXPORTED = ["pdnqp_create", "pdnqp_create_ex", "pdnqp_destroy", "pdnqp_solve", "pdnqp_get", "pdnqp_set_start",
+            "pdnqp_set_param", "pdnqp_get_param", "pdnqp_dims", "pdnqp_last_error", "pdnqp_debug_inner",
+            "pdnqp_replay_kernel", "pdnqp_kernel_bytes"]
+
+
+class pdnqp_csr(C.Structure):
+    _fields_ = [("n_rows", C.c_int32), ("n_cols", C.c_int32), ("nnz", C.c_int64),
+                ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("val", C.c_void_p)]
+
+
+class pdnqp_residuals(C.Structure):
+    _fields_ = [("r_p", C.c_double), ("r_d", C.c_double), ("s_p", C.c_double), ("s_d", C.c_double),
+                ("rel_kkt", C.c_double), ("outer_iters", C.c_int64), ("inner_iters", C.c_int64),
+                ("trials", C.c_int64), ("restarts", C.c_int64), ("kkt_passes", C.c_int64),
+                ("solve_seconds", C.c_double), ("gamma", C.c_double), ("lambda_min", C.c_double),
+                ("obj", C.c_double)]
+
+
+class pdnqp_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p)]
+
+
+class PdnqpError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libpdnqp.so (build it first with paper_2609_19557_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise PdnqpError(f"{p} not found: build the CUDA library first (python -m paper_2609_19557_gb300.build)")
+    L = C.CDLL(p)
+    vp, ip = C.c_void_p, C.c_int
+    L.pdnqp_create.argtypes = [C.POINTER(vp), C.POINTER(pdnqp_csr), vp, C.POINTER(pdnqp_csr), vp, vp, vp, vp]
+    L.pdnqp_create_ex.argtypes = L.pdnqp_create.argtypes + [C.POINTER(pdnqp_options)]
+    L.pdnqp_destroy.argtypes = [vp]
+    L.pdnqp_destroy.restype = None
+    L.pdnqp_solve.argtypes = [vp, C.c_double, C.c_double]
+    L.pdnqp_get.argtypes = [vp, vp, vp, C.POINTER(pdnqp_residuals)]
+    L.pdnqp_set_start.argtypes = [vp, vp, vp]
+    L.pdnqp_set_param.argtypes = [vp, C.c_char_p, C.c_double]
+    L.pdnqp_get_param.argtypes = [vp, C.c_char_p, C.POINTER(C.c_double)]
+    L.pdnqp_dims.argtypes = [vp, vp]
+    L.pdnqp_last_error.argtypes = [vp]
+    L.pdnqp_last_error.restype = C.c_char_p
+    L.pdnqp_debug_inner.argtypes = [vp, ip, vp, vp]
+    L.pdnqp_replay_kernel.argtypes = [vp, ip, ip]
+    L.pdnqp_kernel_bytes.argtypes = [vp, ip, C.POINTER(C.c_double)]
+    for name in EXPORTED:
+        if not hasattr(L, name):
+            raise PdnqpError(f"{p} does not export {name}")
+    _lib = L
+    return L
+
+
+def _csr(M, keep):
+    M = M.tocsr()
+    rp = np.ascontiguousarray(M.indptr, dtype=np.int32)
+    ci = np.ascontiguousarray(M.indices, dtype=np.int32)
+    v = np.ascontiguousarray(M.data, dtype=np.float64)
+    keep += [rp, ci, v]
+    return pdnqp_csr(M.shape[0], M.shape[1], int(v.size), rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
+
+
+def _f64(a, keep):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    keep.append(a)
+    return a.ctypes.data
+
+
+def _check(h, rc):
+    if rc < 0:
+        msg = load().pdnqp_last_error(h)
+        raise PdnqpError(f"pdnqp error {rc}: {msg.decode() if msg else ''}")
+    return rc
+
+
+class Handle:
+    """Owns one pdnqp_t (destroyed on close / garbage collection)."""
+
+    def __init__(self, ptr, n, m):
+        self.ptr, self.n, self.m = ptr, n, m
+
+    def close(self):
+        if self.ptr:
+            load().pdnqp_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pdnqp_create(Q, c, A, l_c, u_c, l_x, u_x, precision: int = PDNQP_FP64, device: int = -1, stream=None) -> Handle:
+    """Q, A: scipy.sparse matrices (Q symmetric, both triangles); vectors: array-likes."""
+    L = load()
+    keep = []
+    q = _csr(Q, keep)
+    a = _csr(A, keep) if A is not None and A.shape[0] > 0 else None
+    opt = pdnqp_options(int(precision), int(device), C.c_void_p(int(stream)) if stream else None)
+    h = C.c_void_p()
+    m = A.shape[0] if A is not None else 0
+    rc = L.pdnqp_create_ex(C.byref(h), C.byref(q), _f64(c, keep), C.byref(a) if a is not None else None,
+                           _f64(l_c, keep) if m else None, _f64(u_c, keep) if m else None, _f64(l_x, keep),
+                           _f64(u_x, keep), C.byref(opt))
+    _check(None, rc)
+    return Handle(h.value, Q.shape[0], m)
+
+
+def pdnqp_destroy(h: Handle):
+    h.close()
+
+
+def pdnqp_solve(h: Handle, eps_abs: float, eps_rel: float) -> int:
+    return _check(h.ptr, load().pdnqp_solve(h.ptr, float(eps_abs), float(eps_rel)))
+
+
+def pdnqp_get(h: Handle):
+    """Returns (x, y, residuals-dict)."""
+    x = np.zeros(h.n)
+    y = np.zeros(h.m)
+    r = pdnqp_residuals()
+    _check(h.ptr, load().pdnqp_get(h.ptr, x.ctypes.data, y.ctypes.data if h.m else None, C.byref(r)))
+    return x, y, {f[0]: getattr(r, f[0]) for f in pdnqp_residuals._fields_}
+
+
+def pdnqp_set_start(h: Handle, x0=None, y0=None):
+    keep = []
+    _check(h.ptr, load().pdnqp_set_start(h.ptr, _f64(x0, keep) if x0 is not None else None,
+                                         _f64(y0, keep) if y0 is not None else None))
+
+
+def pdnqp_set_param(h: Handle, name: str, value: float):
+    _check(h.ptr, load().pdnqp_set_param(h.ptr, name.encode(), float(value)))
+
+
+def pdnqp_get_param(h: Handle, name: str) -> float:
+    v = C.c_double()
+    _check(h.ptr, load().pdnqp_get_param(h.ptr, name.encode(), C.byref(v)))
+    return v.value
+
+
+def pdnqp_dims(h: Handle):
+    out = np.zeros(5, dtype=np.int64)
+    _check(h.ptr, load().pdnqp_dims(h.ptr, out.ctypes.data))
+    return dict(n=int(out[0]), m=int(out[1]), mE=int(out[2]), mI=int(out[3]), nnz_q=int(out[4]))
+
+
+def pdnqp_last_error(h: Handle | None = None) -> str:
+    s = load().pdnqp_last_error(h.ptr if h else None)
+    return s.decode() if s else ""
+
+
+def pdnqp_debug_inner(h: Handle, checkpoints):
+    """Snapshots of the first inner solve (see include/pdnqp.h) as dicts."""
+    d = pdnqp_dims(h)
+    n, m, mI = d["n"], d["m"], d["mI"]
+    dw = n + mI + m
+    L = 2 * (dw + m) + SNAP_SCALARS
+    ck = np.ascontiguousarray(checkpoints, dtype=np.int64)
+    out = np.zeros(L * ck.size)
+    got = _check(h.ptr, load().pdnqp_debug_inner(h.ptr, int(ck.size), ck.ctypes.data, out.ctypes.data))
+    snaps = []
+    for i in range(got):
+        v = out[i * L:(i + 1) * L]
+        snaps.append(dict(w=v[:dw], y=v[dw:dw + m], wbar=v[dw + m:2 * dw + m], ybar=v[2 * dw + m:2 * dw + 2 * m],
+                          omega=v[-8], kappa=v[-7], t=int(v[-6]), t_total=int(v[-5]), trials=int(v[-4]),
+                          restarts=int(v[-3]), kkt_restart=v[-2], kkt_last=v[-1]))
+    return snaps
+
+
+def pdnqp_replay_kernel(h: Handle, which: int, reps: int):
+    _check(h.ptr, load().pdnqp_replay_kernel(h.ptr, int(which), int(reps)))
+
+
+def pdnqp_kernel_bytes(h: Handle, which: int) -> float:
+    v = C.c_double()
+    _check(h.ptr, load().pdnqp_kernel_bytes(h.ptr, int(which), C.byref(v)))
+    return v.value
+
+
+def create_from_instance(inst: dict, precision: int = PDNQP_FP64, stream=None) -> Handle:
+    """Convenience: handle for an instance dict as produced by instances.py."""
+    return pdnqp_create(inst["Q"], inst["c"], inst["A"], inst["l_c"], inst["u_c"], inst["l_x"], inst["u_x"],
+                        precision=precision, stream=stream)
