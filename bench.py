@@ -1,0 +1,335 @@
+"""Benchmark of the PDNQP rAPDHG hot path on one GB300 (or N replicas).
+
+Workload: the 1M-variable synthetic nonconvex QP (n = 1,000,000, m = 500,000,
+Q ~ 5M nnz banded + random, A ~ 4M nnz, box [-1, 1], two-sided rows).
+
+A step is one pass of the whole hot path: pdnqp_solve from the start point
+with a fixed budget of accepted inner iterations (setup of each inner solve,
+trial/accept/average/check/restart iterations, outer multiplier and penalty
+updates).  `value` is accepted rAPDHG inner iterations per second over the
+timed steps, all ranks (replicas only: each rank solves its own seeded
+instance, no data-path collective).  Inputs are larger than L2 (129 MB), so
+no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       [--precision 32|64] [--budget B] [--ttk SECONDS]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rAPDHG iters/s & time-to-1e-4 KKT (1M-var QP), %HBM peak, vs plain FP64 form"
+WORKLOAD = "synthetic nonconvex QP n=1e6 m=5e5 (Q 5M nnz band+random, A 4M nnz, box [-1,1])"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    p.add_argument("--budget", type=int, default=2000, help="accepted inner iterations per step")
+    p.add_argument("--ttk", type=float, default=0.0, help="also time a solve to rel-KKT 1e-4 (cap in seconds)")
+    p.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison leg")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU (oracle) baseline leg")
+    p.add_argument("--n", type=int, default=1_000_000)
+    p.add_argument("--m", type=int, default=500_000)
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_instance(args, seed):
+    from paper_2609_19557_gb300 import instances as I
+    return I.large_qp(seed, n=args.n, m=args.m)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def run_native(args):
+    import torch
+
+    from paper_2609_19557_gb300 import build as B
+    from paper_2609_19557_gb300 import pdnqp as P
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    P.load()
+    inst = make_instance(args, seed=rank)
+    stream = torch.cuda.current_stream()
+    h = P.create_from_instance(inst, precision=args.precision, stream=stream.cuda_stream)
+    P.pdnqp_set_param(h, "iter_budget", args.budget)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        P.pdnqp_solve(h, 1e-4, 1e-4)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = 0
+    launches = 0
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        P.pdnqp_solve(h, 1e-4, 1e-4)
+        _, _, r = P.pdnqp_get(h)
+        iters += r["inner_iters"]
+        launches += r["kernel_launches"]
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    dt = ev0.elapsed_time(ev1) / 1e3
+    t_max = dt
+    it_all = iters
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dt], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        c = torch.tensor([float(iters)], device="cuda")
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        it_all = int(c.item())
+    value = it_all / t_max
+
+    # Dominant kernel: fused Q / A^T SpMV + acceptance terms, replayed on the same stream.
+    peak, peak_src = measured_peaks()
+    kb = P.pdnqp_kernel_bytes(h, 0)
+    P.pdnqp_replay_kernel(h, 0, 5)
+    reps = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    P.pdnqp_replay_kernel(h, 0, reps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    kdur = e0.elapsed_time(e1) / 1e3 / reps
+    achieved = kb / kdur / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", f"traffic_cols_fp{args.precision}.json")
+    if os.path.exists(tr_path):
+        traffic = json.load(open(tr_path)).get("bytes_per_launch")
+
+    # End to end through the public API with host buffers: create (H2D of the
+    # problem) + solve + get (D2H of x, y) inside the timed region.
+    h2d = sum(a.nbytes for a in (inst["Q"].data, inst["Q"].indices, inst["Q"].indptr, inst["A"].data,
+                                 inst["A"].indices, inst["A"].indptr, inst["c"], inst["l_c"], inst["u_c"],
+                                 inst["l_x"], inst["u_x"]))
+    d2h = 8 * (inst["Q"].shape[0] + inst["A"].shape[0])
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(e2e_steps):
+        h2 = P.create_from_instance(inst, precision=args.precision, stream=stream.cuda_stream)
+        P.pdnqp_set_param(h2, "iter_budget", args.budget)
+        P.pdnqp_solve(h2, 1e-4, 1e-4)
+        x, y, r2 = P.pdnqp_get(h2)
+        e2e_iters += r2["inner_iters"]
+        h2.close()
+    barrier()
+    e2e_dt = time.perf_counter() - t0
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_dt], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_dt = float(t.item())
+        c = torch.tensor([float(e2e_iters)], device="cuda")
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        e2e_iters = int(c.item())
+
+    # Plain FP64 form on the same GPU (the comparison the metric names).
+    compare = None
+    if not args.no_compare and args.precision != 64:
+        h64 = P.create_from_instance(inst, precision=64, stream=stream.cuda_stream)
+        P.pdnqp_set_param(h64, "iter_budget", args.budget)
+        P.pdnqp_solve(h64, 1e-4, 1e-4)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        it64 = 0
+        for _ in range(max(1, args.steps // 2)):
+            P.pdnqp_solve(h64, 1e-4, 1e-4)
+            it64 += P.pdnqp_get(h64)[2]["inner_iters"]
+        a1.record(stream)
+        torch.cuda.synchronize()
+        compare = {"fp64_iters_per_s": it64 / (a0.elapsed_time(a1) / 1e3)}
+        h64.close()
+
+    ttk = None
+    if args.ttk > 0 and rank == 0:
+        h3 = P.create_from_instance(inst, precision=args.precision, stream=stream.cuda_stream)
+        P.pdnqp_set_param(h3, "time_limit", args.ttk)
+        st = P.pdnqp_solve(h3, 1e-4, 1e-4)
+        _, _, r3 = P.pdnqp_get(h3)
+        ttk = {"status": P.STATUS_NAMES[st], "seconds": r3["solve_seconds"], "rel_kkt": r3["rel_kkt"],
+               "outer_iters": r3["outer_iters"], "inner_iters": r3["inner_iters"]}
+        h3.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(inst)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == 32 else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": args.n, "m": args.m, "step": f"pdnqp_solve with {args.budget} "
+                       "accepted inner iterations", "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "precision": "FP32-bulk" if args.precision == 32 else "plain FP64"},
+            "e2e": {"value": e2e_iters / e2e_dt, "unit": "iters/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_cols (Q and A^T SpMV + acceptance)",
+                         "peak_source": peak_src, "kernel_us": kdur * 1e6},
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        if compare:
+            out["vs_plain_fp64"] = {"fp64_iters_per_s": compare["fp64_iters_per_s"],
+                                    "speedup": value / ws / compare["fp64_iters_per_s"]}
+        if ttk:
+            out["time_to_1e-4"] = ttk
+        print(json.dumps(out), flush=True)
+    h.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(inst, first=2, last=6):
+    """The oracle as it stands, single-threaded, on a bounded sample of the same
+    workload: accepted inner iterations per second between two checkpoints of
+    the first inner solve."""
+    from oracle import oracle as O
+    O.build()
+    times, setup = O.debug_inner_timed(inst, [first, last])
+    if len(times) < 2:
+        return None
+    rate = (last - first) / (times[1] - times[0])
+    return {"value": rate, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"accepted inner iterations {first}..{last} of the first inner solve (setup {setup:.1f} s excluded)"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, same workload and metric."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    inst = make_instance(args, seed=0)
+    per_step = 1  # accepted inner iterations per step (the oracle needs ~seconds per iteration here)
+    ck = [per_step * (k + 1) for k in range(args.warmup + args.steps)]
+    times, setup = O.debug_inner_timed(inst, ck)
+    t_w = times[args.warmup - 1] if args.warmup > 0 else 0.0
+    dt = times[-1] - t_w
+    value = per_step * args.steps / dt
+    out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "n": args.n, "m": args.m,
+                      "step": f"{per_step} accepted inner iteration(s) of the FP64 oracle"},
+           "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{args.steps} timed steps after {args.warmup} warm-up steps; setup "
+                                      f"{setup:.1f} s excluded"},
+           "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_native(a)

@@ -93,6 +93,7 @@ typedef struct {
   double gamma;              /* proximal step of Eq. R-choice (scaled problem) */
   double lambda_min;         /* Lanczos estimate of lambda_min of the scaled Q */
   double obj;                /* c'x + 1/2 x'Qx at the returned x */
+  int64_t kernel_launches;   /* CUDA kernels launched by the last pdnqp_solve (graph nodes included) */
 } pdnqp_residuals;
 
 /* Creation options (pdnqp_create uses precision = PDNQP_FP64, device = current,
@@ -144,7 +145,10 @@ PDNQP_API int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0);
  * ruiz_outer (applies to the next pdnqp_create only; read-only here),
  * ruiz_inner, k_chk, beta_suff, beta_nec, beta_art, rej_limit, kappa_shrink,
  * delta_sigma, sigma_max, tol_floor, gamma (override, > 0; setting it
- * replaces the Lanczos choice), chunk (trial slots per CUDA-graph launch).
+ * replaces the Lanczos choice), chunk (trial slots per CUDA-graph launch),
+ * iter_budget (cap on accepted inner iterations per pdnqp_solve, summed over
+ * outer iterations; ITER_LIMIT when reached), g_rows / g_cols (lanes per CSR
+ * row in the SpMV kernels, 0 = from the mean row length).
  * Returns PDNQP_ERR_ARG for an unknown name or an out-of-range value. */
 PDNQP_API int pdnqp_set_param(pdnqp_t *h, const char *name, double value);
 PDNQP_API int pdnqp_get_param(const pdnqp_t *h, const char *name, double *value);

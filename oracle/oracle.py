@@ -89,6 +89,7 @@ def lib():
             L.or_tridiag_min_eig.restype = C.c_double
             L.or_ruiz_outer.argtypes = [C.c_int, C.c_int] + [C.c_void_p] * 6 + [C.c_int, C.c_void_p, C.c_void_p]
             L.or_project.argtypes = [C.c_int] + [C.c_void_p] * 4
+            L.or_debug_inner_timed.argtypes = [dp(_Problem), dp(_Params), C.c_int] + [C.c_void_p] * 4
             _lib = L
     return _lib
 
@@ -270,3 +271,20 @@ def project(v, lo, hi):
     out = np.zeros_like(v)
     lib().or_project(v.size, _ptr(v), _ptr(lo), _ptr(hi), _ptr(out))
     return out
+
+
+def debug_inner_timed(inst: dict, checkpoints, x0=None, **params):
+    """Wall-clock seconds (from the first inner iteration) at each checkpoint, and the setup time."""
+    P = Problem(inst, x0)
+    prm = default_params(**params)
+    info = setup_info(inst, x0, **params) if P.n <= 200_000 else None
+    mE = info["mE"] if info else None
+    ck = np.ascontiguousarray(sorted(checkpoints), dtype=np.int64)
+    # snapshot buffer sized for the largest possible layout (dw <= n + 2m)
+    L = 2 * (P.n + 3 * P.m) + SNAP_SCALARS
+    out = np.zeros(L * len(ck))
+    times = np.zeros(len(ck))
+    setup = np.zeros(1)
+    got = lib().or_debug_inner_timed(P.ref(), C.byref(prm), len(ck), _ptr(ck), _ptr(out), _ptr(times), _ptr(setup))
+    del mE
+    return times[:max(got, 0)], float(setup[0])

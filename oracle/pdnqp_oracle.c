@@ -36,7 +36,8 @@
  *   - Objective scalar c_s = 1/max(1, ||D Q D||_inf, ||D c||_inf) with the
  *     induced (max row-sum) norm for the matrix.
  *   - Initial penalties follow QPALM's formula; the growth factor is capped and
- *     rows already within the primal target are not penalised further.
+ *     penalties stop growing once the primal part of the termination test holds.
+ *   - The center-update tolerances never drop below the final tolerances.
  *   - Outer termination is evaluated on the unscaled problem.
  *
  * Parity pins are in the test-suite: brute-force active-set enumeration,
@@ -635,11 +636,14 @@ typedef struct {
   double *snap;
   int next_ckpt;
   int ignore_convergence;
+  double *times; /* optional: wall-clock seconds at each snapshot */
 } dbg_t;
 
 typedef struct {
   long long trials, accepted, restarts;
 } ctr_t;
+
+static double now_seconds(void);
 
 static void take_snapshot(const iqp_t *I, dbg_t *D, const double *w, const double *y, const double *wb,
                           const double *yb, double omega, double kappa, long long t, long long ttot,
@@ -654,6 +658,7 @@ static void take_snapshot(const iqp_t *I, dbg_t *D, const double *w, const doubl
   double *sc = o + 2 * (size_t)(dw + m);
   sc[0] = omega; sc[1] = kappa; sc[2] = (double)t; sc[3] = (double)ttot;
   sc[4] = (double)trials; sc[5] = (double)restarts; sc[6] = krest; sc[7] = klast;
+  if (D->times) D->times[D->next_ckpt] = now_seconds();
   D->next_ckpt++;
 }
 
@@ -930,13 +935,13 @@ int or_solve(const or_problem *P, const or_params *prm, double *x_out, double *y
     if (un.rp <= prm->eps_abs + prm->eps_rel * un.sp && un.rd <= prm->eps_abs + prm->eps_rel * un.sd) {
       status = OR_SOLVED; ++k; break;
     }
-    /* Eq. penalty-trigger-eq: row-wise increase when the residual did not drop enough.
-     * Rows whose residual already meets the primal target eps_a + eps_r s_p are left alone. */
+    /* Eq. penalty-trigger-eq: row-wise increase when the residual did not drop enough,
+     * as long as the primal part of Eq. outer-termination is not met yet. */
     double rn = norm_inf(r, m);
-    double rtarget = prm->eps_abs + prm->eps_rel * sc.sp;
+    int primal_ok = un.rp <= prm->eps_abs + prm->eps_rel * un.sp && sc.rp <= prm->eps_abs + prm->eps_rel * sc.sp;
     for (int j = 0; j < m; ++j) {
       int active = j < S->mE || T.lam[j] != 0.0;
-      if (active && fabs(r[j]) > prm->theta_sigma * fabs(T.rprev[j]) && fabs(r[j]) > rtarget && rn > 0.0)
+      if (active && !primal_ok && fabs(r[j]) > prm->theta_sigma * fabs(T.rprev[j]) && rn > 0.0)
         T.sig[j] = dmin(prm->sigma_max, T.sig[j] * dmax(1.0, prm->delta_sigma * fabs(r[j]) / rn));
       T.rprev[j] = r[j];
     }
@@ -957,7 +962,8 @@ int or_solve(const or_problem *P, const or_params *prm, double *x_out, double *y
     /* Eq. center-update / center-tolerance-update. */
     if (sc.rp <= eak + erk * sc.sp) {
       memcpy(T.z, T.x, sizeof(double) * n);
-      eak *= prm->rho_z; erk *= prm->rho_z;
+      eak = dmax(eak * prm->rho_z, prm->eps_abs);
+      erk = dmax(erk * prm->rho_z, prm->eps_rel);
     }
   }
   /* Unscale and return (Algorithm 3). */
@@ -993,7 +999,7 @@ int or_debug_inner(const or_problem *P, const or_params *prm, int n_ckpt, const 
   setup(P, prm, &T);
   double omega = 1.0;
   ctr_t C = {0, 0, 0};
-  dbg_t D = {n_ckpt, ckpt, snap, 0, 1};
+  dbg_t D = {n_ckpt, ckpt, snap, 0, 1, NULL};
   int st = inner_solve(&T.S, prm, T.z, T.lam, T.sig, T.gamma, 1.0, 1.0, T.x, T.yin, &omega, &C, &D);
   if (gamma_out) *gamma_out = T.gamma;
   state_free(&T);
@@ -1112,4 +1118,24 @@ int or_kkt_check(const or_problem *P, const double *x, const double *lam, double
   free(ax); free(qx); free(atl);
   ocsr_free(&At);
   return 0;
+}
+
+/* Same as or_debug_inner, also returning the wall-clock time of each
+ * snapshot relative to the start of the inner iterations (times[k]), for the
+ * CPU baseline.  setup_seconds receives the time spent before the first
+ * inner iteration. */
+int or_debug_inner_timed(const or_problem *P, const or_params *prm, int n_ckpt, const long long *ckpt, double *snap,
+                         double *times, double *setup_seconds) {
+  double t0 = now_seconds();
+  state_t T;
+  setup(P, prm, &T);
+  double omega = 1.0;
+  ctr_t C = {0, 0, 0};
+  dbg_t D = {n_ckpt, ckpt, snap, 0, 1, times};
+  double t1 = now_seconds();
+  int st = inner_solve(&T.S, prm, T.z, T.lam, T.sig, T.gamma, 1.0, 1.0, T.x, T.yin, &omega, &C, &D);
+  for (int k = 0; k < D.next_ckpt; ++k) times[k] -= t1;
+  *setup_seconds = t1 - t0;
+  state_free(&T);
+  return st == IN_NUMERICAL_ERROR ? -1 : D.next_ckpt;
 }

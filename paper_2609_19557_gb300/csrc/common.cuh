@@ -170,6 +170,86 @@ __device__ __forceinline__ Acc row_max(const int *__restrict__ rp, const int *__
   return group_max<G, Acc>(a);
 }
 
+
+// Warp tiles of 32 consecutive rows: lane l owns row tile + l for the
+// epilogue (all lanes active, coalesced per-row loads and stores), while the
+// row dot products are computed by groups of G lanes in G passes of 32/G rows
+// each, and the result of each row is shuffled to the lane that owns it.
+struct TileIter {
+  int lane;
+  long long first, step;
+  __device__ __forceinline__ TileIter() {
+    lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    first = gw * 32;
+    step = nw * 32;
+  }
+};
+
+template <typename Acc>
+__device__ __forceinline__ Acc shfl_any(Acc v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+
+// Lane l of the warp returns sum_{k in row(tile + l)} f(col_k, val_k) (0 past
+// nrows).  rp is read once per tile (coalesced) and distributed by shuffles.
+template <int G, typename Acc, typename T, typename F>
+__device__ __forceinline__ Acc tile_row_sum(const int *__restrict__ rp, const int *__restrict__ ci,
+                                            const T *__restrict__ val, long long tile, long long nrows, F f) {
+  constexpr int RPP = 32 / G;  // rows per pass
+  const int lane = threadIdx.x & 31;
+  const int gid = lane / G, lg = lane & (G - 1);
+  const long long my = tile + lane;
+  int rb = 0, re = 0;
+  if (my < nrows) {
+    rb = rp[my];
+    re = rp[my + 1];
+  }
+  Acc mine = Acc(0);
+#pragma unroll
+  for (int pass = 0; pass < G; ++pass) {
+    const int owner = pass * RPP + gid;  // lane that owns the row this group works on
+    const int b = __shfl_sync(0xffffffffu, rb, owner);
+    const int e = __shfl_sync(0xffffffffu, re, owner);
+    Acc a = Acc(0);
+    for (int k = b + lg; k < e; k += G) a += f(ci[k], val[k]);
+    a = group_sum<G, Acc>(a);
+    const int src = (lane - pass * RPP) * G;
+    const Acc v = shfl_any<Acc>(a, src & 31);
+    if (lane >= pass * RPP && lane < (pass + 1) * RPP) mine = v;
+  }
+  return mine;
+}
+
+template <int G, typename Acc, typename T, typename F>
+__device__ __forceinline__ Acc tile_row_max(const int *__restrict__ rp, const int *__restrict__ ci,
+                                            const T *__restrict__ val, long long tile, long long nrows, F f) {
+  constexpr int RPP = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int gid = lane / G, lg = lane & (G - 1);
+  const long long my = tile + lane;
+  int rb = 0, re = 0;
+  if (my < nrows) {
+    rb = rp[my];
+    re = rp[my + 1];
+  }
+  Acc mine = Acc(0);
+#pragma unroll
+  for (int pass = 0; pass < G; ++pass) {
+    const int owner = pass * RPP + gid;
+    const int b = __shfl_sync(0xffffffffu, rb, owner);
+    const int e = __shfl_sync(0xffffffffu, re, owner);
+    Acc a = Acc(0);
+    for (int k = b + lg; k < e; k += G) a = fmax(a, f(ci[k], val[k]));
+    a = group_max<G, Acc>(a);
+    const int src = (lane - pass * RPP) * G;
+    const Acc v = shfl_any<Acc>(a, src & 31);
+    if (lane >= pass * RPP && lane < (pass + 1) * RPP) mine = v;
+  }
+  return mine;
+}
+
 inline int grid_for(long long work_items, int per_block) {
   long long b = (work_items + per_block - 1) / per_block;
   if (b < 1) b = 1;

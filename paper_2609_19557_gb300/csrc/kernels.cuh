@@ -25,10 +25,10 @@ namespace pdq {
 namespace {  // internal linkage: each solver TU owns its kernels
 
 // Rows of the partial-sums array used by each reduction.
-constexpr int P_TR_R = 0;    // trial, row kernel: lhs, rhs_h, rhs_b
-constexpr int P_TR_C = 3;    // trial, column kernel
-constexpr int P_CK_R = 6;    // check, row kernel: 16 quantities
-constexpr int P_CK_C = 22;   // check, column kernel: 16 quantities
+constexpr int P_TR_R = 0;    // trial, row kernel: lhs_tau, lhs_eta, rhs_h, rhs_b
+constexpr int P_TR_C = 4;    // trial, column kernel (same 4)
+constexpr int P_CK_R = 8;    // check, row kernel: 16 quantities
+constexpr int P_CK_C = 24;   // check, column kernel: 16 quantities
 constexpr unsigned CK_MAXMASK = 0x0F0Fu;  // quantities 0-3 and 8-11 of a check are maxima
 
 template <typename T>
@@ -46,10 +46,10 @@ struct Dev {
   Mat<T> H, A, At;  // H = Qbar + gamma^-1 I (x block of H_k), A (rows E then I), A^T
   // n-vectors
   T *x[2], *Hx[2], *Aty[2], *xbar[2], *Hxbar[2];
-  T *qx, *lx, *ux, *taux, *ex, *xst, *Atybar;
+  T *qx, *lx, *ux, *taux, *itaux, *ex, *xst, *Atybar;
   // m-vectors (s is indexed by row; entries of equality rows are unused)
   T *y[2], *s[2], *r[2], *Bw[2], *ybar[2], *sbar[2], *rbar[2];
-  T *eta, *taus, *taur, *es, *er, *dy, *h, *ls, *us, *yst, *sst, *rst, *Bwbar;
+  T *eta, *taus, *taur, *ieta, *itaus, *itaur, *es, *er, *dy, *h, *ls, *us, *yst, *sst, *rst, *Bwbar;
   // FP64 outer data: multipliers lambda and row penalties sigma
   const double *lam, *sig;
   double *part;
@@ -63,6 +63,14 @@ __device__ __forceinline__ T clampv(T v, T lo, T hi) {
   v = v > hi ? hi : v;
   return v;
 }
+
+// Per-thread accumulator of the acceptance sums: FP64 in the FP64 form; in
+// the FP32-bulk form each thread sums its few rows in FP32 and the cross-
+// thread reduction is FP64 (block_reduce_store / final_reduce).
+template <typename T>
+struct SumT {
+  typedef T type;
+};
 
 #define PDNQP_GRID_STRIDE(i, N) \
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)(N); \
@@ -96,7 +104,10 @@ __global__ void __launch_bounds__(kBlock) k_primal(Dev<T> d) {
 
 // Constraint rows: (A x_tr)_j, the s/r blocks of the primal trial, B w_tr,
 // the dual trial y_tr = y + eta (h - B w_tr - beta (B w_tr - B w)), and the
-// row-local terms of the acceptance sums.
+// row-local terms of the acceptance sums.  Steps are used as
+// tau = (kappa / omega) tau0, eta = (kappa omega) eta0; the sums of
+// dw^2 / tau and dy^2 / eta are accumulated with the stored inverses 1/tau0,
+// 1/eta0 and scaled once by omega / kappa and 1 / (kappa omega).
 template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_rows(Dev<T> d) {
   const DevState *st = d.st;
@@ -107,41 +118,38 @@ __global__ void __launch_bounds__(kBlock) k_rows(Dev<T> d) {
   const T beta = T(t / (t + 1.0));
   const T sct = T(st->kappa / st->omega), sce = T(st->kappa * st->omega);
   const T *__restrict__ xt = d.x[nx];
-  double L = 0.0, RH = 0.0, RB = 0.0;
-  GroupIter<G> it;
-  for (long long base = it.first; base < d.m; base += it.step) {
-    const long long j = base + it.sub;
-    const bool valid = j < d.m;
-    const T ax = row_sum<G, T>(d.A.rp, d.A.ci, d.A.val, j, valid, it.lane_g,
-                               [&](int k, T a) { return a * xt[k]; });
-    if (valid && it.lane_g == 0) {
+  T Lt = T(0), Le = T(0), RH = T(0), RB = T(0);
+  TileIter ti;
+  for (long long tile = ti.first; tile < d.m; tile += ti.step) {
+    const T ax = tile_row_sum<G, T>(d.A.rp, d.A.ci, d.A.val, tile, d.m, [&](int k, T a) { return a * xt[k]; });
+    const long long j = tile + ti.lane;
+    if (j < d.m) {
       const T y = d.y[cur][j], r = d.r[cur][j], rb = d.rbar[ab][j];
       const T lam = T(d.lam[j]), sig = T(d.sig[j]);
-      const T tr = sct * d.taur[j];
-      const T rt = r - tr * (lam + sig * (oma * rb + alpha * r) + y);
-      T bwt = ax - rt, ds = T(0), ts = T(1);
+      const T rt = r - (sct * d.taur[j]) * (lam + sig * (oma * rb + alpha * r) + y);
+      T bwt = ax - rt, ds = T(0);
       if (j >= d.mE) {
         const T s = d.s[cur][j];
-        ts = sct * d.taus[j];
-        const T stv = clampv<T>(s - ts * y, d.ls[j], d.us[j]);
+        const T stv = clampv<T>(s - (sct * d.taus[j]) * y, d.ls[j], d.us[j]);
         d.s[nx][j] = stv;
         bwt -= stv;
         ds = stv - s;
+        Lt += ds * ds * d.itaus[j];
       }
       const T bw = d.Bw[cur][j];
-      const T et = sce * d.eta[j];
-      const T yt = y + et * (d.h[j] - bwt - beta * (bwt - bw));
+      const T yt = y + (sce * d.eta[j]) * (d.h[j] - bwt - beta * (bwt - bw));
       d.r[nx][j] = rt;
       d.Bw[nx][j] = bwt;
       d.y[nx][j] = yt;
-      const double dr = double(rt - r), dyv = double(yt - y), dsv = double(ds);
-      L += dr * dr / double(tr) + dyv * dyv / double(et) + (j >= d.mE ? dsv * dsv / double(ts) : 0.0);
-      RH += fabs(dr * double(sig) * dr);
-      RB += fabs(dsv * dyv) + fabs(dr * dyv);
+      const T dr = rt - r, dyv = yt - y;
+      Lt += dr * dr * d.itaur[j];
+      Le += dyv * dyv * d.ieta[j];
+      RH += fabs(dr * sig * dr);
+      RB += fabs(ds * dyv) + fabs(dr * dyv);
     }
   }
-  double v[3] = {L, RH, RB};
-  block_reduce_store<3>(v, 0u, d.part + P_TR_R * kMaxBlocks);
+  double v[4] = {double(Lt), double(Le), double(RH), double(RB)};
+  block_reduce_store<4>(v, 0u, d.part + P_TR_R * kMaxBlocks);
 }
 
 // Variable rows: (H x_tr)_i and (A' y_tr)_i (the products with Q and A^T),
@@ -151,31 +159,27 @@ __global__ void __launch_bounds__(kBlock) k_cols(Dev<T> d) {
   const DevState *st = d.st;
   if (st->status != ST_RUNNING) return;
   const int cur = st->cur, nx = 1 - cur;
-  const T sct = T(st->kappa / st->omega);
   const T *__restrict__ xt = d.x[nx];
   const T *__restrict__ yt = d.y[nx];
-  double L = 0.0, RH = 0.0, RB = 0.0;
-  GroupIter<G> it;
-  for (long long base = it.first; base < d.n; base += it.step) {
-    const long long i = base + it.sub;
-    const bool valid = i < d.n;
-    const T hx = row_sum<G, T>(d.H.rp, d.H.ci, d.H.val, i, valid, it.lane_g,
-                               [&](int k, T a) { return a * xt[k]; });
-    const T aty = row_sum<G, T>(d.At.rp, d.At.ci, d.At.val, i, valid, it.lane_g,
-                                [&](int k, T a) { return a * yt[k]; });
-    if (valid && it.lane_g == 0) {
+  T Lt = T(0), RH = T(0), RB = T(0);
+  TileIter ti;
+  for (long long tile = ti.first; tile < d.n; tile += ti.step) {
+    const T hx = tile_row_sum<G, T>(d.H.rp, d.H.ci, d.H.val, tile, d.n, [&](int k, T a) { return a * xt[k]; });
+    const T aty = tile_row_sum<G, T>(d.At.rp, d.At.ci, d.At.val, tile, d.n, [&](int k, T a) { return a * yt[k]; });
+    const long long i = tile + ti.lane;
+    if (i < d.n) {
       d.Hx[nx][i] = hx;
       d.Aty[nx][i] = aty;
-      const double dx = double(xt[i] - d.x[cur][i]);
-      const double dh = double(hx - d.Hx[cur][i]);
-      const double da = double(aty - d.Aty[cur][i]);
-      L += dx * dx / double(sct * d.taux[i]);
+      const T dx = xt[i] - d.x[cur][i];
+      const T dh = hx - d.Hx[cur][i];
+      const T da = aty - d.Aty[cur][i];
+      Lt += dx * dx * d.itaux[i];
       RH += fabs(dx * dh);
       RB += fabs(dx * da);
     }
   }
-  double v[3] = {L, RH, RB};
-  block_reduce_store<3>(v, 0u, d.part + P_TR_C * kMaxBlocks);
+  double v[4] = {double(Lt), 0.0, double(RH), double(RB)};
+  block_reduce_store<4>(v, 0u, d.part + P_TR_C * kMaxBlocks);
 }
 
 // Acceptance decision (single block, deterministic order).  On acceptance the
@@ -183,9 +187,9 @@ __global__ void __launch_bounds__(kBlock) k_cols(Dev<T> d) {
 // are shrunk through kappa.
 __global__ void __launch_bounds__(kRedThreads) k_decide(DevState *st, const double *part, int nb_r, int nb_c) {
   if (st->status != ST_RUNNING) return;
-  double a[3], b[3];
-  final_reduce<3>(part + P_TR_R * kMaxBlocks, nb_r, 0u, a);
-  final_reduce<3>(part + P_TR_C * kMaxBlocks, nb_c, 0u, b);
+  double a[4], b[4];
+  final_reduce<4>(part + P_TR_R * kMaxBlocks, nb_r, 0u, a);
+  final_reduce<4>(part + P_TR_C * kMaxBlocks, nb_c, 0u, b);
   if (threadIdx.x != 0) return;
   // Commit the averages computed after the previous acceptance.
   st->acur ^= st->accepted;
@@ -193,7 +197,9 @@ __global__ void __launch_bounds__(kRedThreads) k_decide(DevState *st, const doub
   st->restart_flag = 0;
   st->check_due = 0;
   st->trials += 1;
-  const double lhs = a[0] + b[0], rh = a[1] + b[1], rb = a[2] + b[2];
+  const double om = st->omega, ka = st->kappa;
+  const double lhs = (om / ka) * (a[0] + b[0]) + (a[1] + b[1]) / (ka * om);
+  const double rh = a[2] + b[2], rb = a[3] + b[3];
   if (!isfinite(lhs) || !isfinite(rh) || !isfinite(rb)) {
     st->status = ST_NUMERICAL_ERROR;
     return;
@@ -292,14 +298,13 @@ __global__ void __launch_bounds__(kBlock) k_check_rows(Dev<T> d, int mode) {
   double q[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) q[k] = 0.0;
-  GroupIter<G> it;
-  for (long long base = it.first; base < d.m; base += it.step) {
-    const long long j = base + it.sub;
-    const bool valid = j < d.m;
+  TileIter ti;
+  for (long long tile = ti.first; tile < d.m; tile += ti.step) {
     T axb = T(0);
     if (mode == 0)
-      axb = row_sum<G, T>(d.A.rp, d.A.ci, d.A.val, j, valid, it.lane_g, [&](int k, T a) { return a * xb[k]; });
-    if (valid && it.lane_g == 0) {
+      axb = tile_row_sum<G, T>(d.A.rp, d.A.ci, d.A.val, tile, d.m, [&](int k, T a) { return a * xb[k]; });
+    const long long j = tile + ti.lane;
+    if (j < d.m) {
       const bool ineq = j >= d.mE;
       const T h = d.h[j], lam = T(d.lam[j]), sig = T(d.sig[j]);
       const T ls = ineq ? d.ls[j] : T(0), us = ineq ? d.us[j] : T(0), es = ineq ? d.es[j] : T(1);
@@ -348,14 +353,13 @@ __global__ void __launch_bounds__(kBlock) k_check_cols(Dev<T> d, int mode) {
   double q[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) q[k] = 0.0;
-  GroupIter<G> it;
-  for (long long base = it.first; base < d.n; base += it.step) {
-    const long long i = base + it.sub;
-    const bool valid = i < d.n;
+  TileIter ti;
+  for (long long tile = ti.first; tile < d.n; tile += ti.step) {
     T atyb = T(0);
     if (mode == 0)
-      atyb = row_sum<G, T>(d.At.rp, d.At.ci, d.At.val, i, valid, it.lane_g, [&](int k, T a) { return a * yb[k]; });
-    if (valid && it.lane_g == 0) {
+      atyb = tile_row_sum<G, T>(d.At.rp, d.At.ci, d.At.val, tile, d.n, [&](int k, T a) { return a * yb[k]; });
+    const long long i = tile + ti.lane;
+    if (i < d.n) {
       const T qx = d.qx[i], lx = d.lx[i], ux = d.ux[i], ex = d.ex[i], xst = d.xst[i];
       col_cand<T>(q, d.x[cur][i], d.Hx[cur][i], d.Aty[cur][i], qx, lx, ux, ex, xst);
       if (mode == 0) {
@@ -480,12 +484,11 @@ template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_warm_rows(Dev<T> d) {
   const int cur = d.st->cur;
   const T *__restrict__ x = d.x[cur];
-  GroupIter<G> it;
-  for (long long base = it.first; base < d.m; base += it.step) {
-    const long long j = base + it.sub;
-    const bool valid = j < d.m;
-    const T ax = row_sum<G, T>(d.A.rp, d.A.ci, d.A.val, j, valid, it.lane_g, [&](int k, T a) { return a * x[k]; });
-    if (valid && it.lane_g == 0) {
+  TileIter ti;
+  for (long long tile = ti.first; tile < d.m; tile += ti.step) {
+    const T ax = tile_row_sum<G, T>(d.A.rp, d.A.ci, d.A.val, tile, d.m, [&](int k, T a) { return a * x[k]; });
+    const long long j = tile + ti.lane;
+    if (j < d.m) {
       T r, bw;
       if (j >= d.mE) {
         const T s = clampv<T>(T(double(ax) + d.lam[j] / d.sig[j]), d.ls[j], d.us[j]);
@@ -517,16 +520,15 @@ __global__ void k_iscale_init(Dev<T> d) {
 // max(max_k |e_k H_ki e_i|, max_j |d_j A_ji e_i|).
 template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_iruiz_cols(Dev<T> d, double *cnx) {
-  GroupIter<G> it;
-  for (long long base = it.first; base < d.n; base += it.step) {
-    const long long i = base + it.sub;
-    const bool valid = i < d.n;
-    const double ei = valid ? double(d.ex[i]) : 0.0;
-    const double a = row_max<G, double>(d.H.rp, d.H.ci, d.H.val, i, valid, it.lane_g,
-                                        [&](int k, T v) { return fabs(double(d.ex[k]) * double(v) * ei); });
-    const double b = row_max<G, double>(d.At.rp, d.At.ci, d.At.val, i, valid, it.lane_g,
-                                        [&](int k, T v) { return fabs(double(d.dy[k]) * double(v) * ei); });
-    if (valid && it.lane_g == 0) cnx[i] = fmax(a, b);
+  TileIter ti;
+  for (long long tile = ti.first; tile < d.n; tile += ti.step) {
+    const long long i = tile + ti.lane;
+    // e_i is applied after the reduction (max over k of |e_k H_ki| times e_i).
+    const double a = tile_row_max<G, double>(d.H.rp, d.H.ci, d.H.val, tile, d.n,
+                                             [&](int k, T v) { return fabs(double(d.ex[k]) * double(v)); });
+    const double b = tile_row_max<G, double>(d.At.rp, d.At.ci, d.At.val, tile, d.n,
+                                             [&](int k, T v) { return fabs(double(d.dy[k]) * double(v)); });
+    if (i < d.n) cnx[i] = fmax(a, b) * double(d.ex[i]);
   }
 }
 
@@ -534,16 +536,15 @@ __global__ void __launch_bounds__(kBlock) k_iruiz_cols(Dev<T> d, double *cnx) {
 // d_j e_s (I rows), d_j e_r); s column: d_j e_s; r column: max(e_r^2 sigma_j, d_j e_r).
 template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_iruiz_rows(Dev<T> d, double *rn, double *cns, double *cnr) {
-  GroupIter<G> it;
-  for (long long base = it.first; base < d.m; base += it.step) {
-    const long long j = base + it.sub;
-    const bool valid = j < d.m;
-    const double dj = valid ? double(d.dy[j]) : 0.0;
-    const double a = row_max<G, double>(d.A.rp, d.A.ci, d.A.val, j, valid, it.lane_g,
-                                        [&](int k, T v) { return fabs(dj * double(v) * double(d.ex[k])); });
-    if (valid && it.lane_g == 0) {
+  TileIter ti;
+  for (long long tile = ti.first; tile < d.m; tile += ti.step) {
+    const double a = tile_row_max<G, double>(d.A.rp, d.A.ci, d.A.val, tile, d.m,
+                                             [&](int k, T v) { return fabs(double(v) * double(d.ex[k])); });
+    const long long j = tile + ti.lane;
+    if (j < d.m) {
+      const double dj = double(d.dy[j]);
       const double er = double(d.er[j]);
-      double rowv = fmax(a, dj * er);
+      double rowv = fmax(a * dj, dj * er);
       if (j >= d.mE) {
         const double es = double(d.es[j]);
         rowv = fmax(rowv, dj * es);
@@ -577,23 +578,23 @@ __global__ void k_iruiz_update(Dev<T> d, const double *cnx, const double *rn, co
 // tau_eff / (kappa / omega) = e^2 * 0.99 / m_w (Eq. diagonal-steps).
 template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_mw_cols(Dev<T> d, double *mwx) {
-  GroupIter<G> it;
-  for (long long base = it.first; base < d.n; base += it.step) {
-    const long long i = base + it.sub;
-    const bool valid = i < d.n;
-    const double ei = valid ? double(d.ex[i]) : 0.0;
-    const double h1 = row_sum<G, double>(d.H.rp, d.H.ci, d.H.val, i, valid, it.lane_g,
-                                         [&](int k, T v) { return fabs(double(d.ex[k]) * double(v) * ei); });
-    const double b1 = row_sum<G, double>(d.At.rp, d.At.ci, d.At.val, i, valid, it.lane_g,
-                                         [&](int k, T v) { return fabs(double(d.dy[k]) * double(v) * ei); });
-    const double b2 = row_sum<G, double>(d.At.rp, d.At.ci, d.At.val, i, valid, it.lane_g, [&](int k, T v) {
-      const double bb = double(d.dy[k]) * double(v) * ei;
+  TileIter ti;
+  for (long long tile = ti.first; tile < d.n; tile += ti.step) {
+    const double h1 = tile_row_sum<G, double>(d.H.rp, d.H.ci, d.H.val, tile, d.n,
+                                              [&](int k, T v) { return fabs(double(d.ex[k]) * double(v)); });
+    const double b1 = tile_row_sum<G, double>(d.At.rp, d.At.ci, d.At.val, tile, d.n,
+                                              [&](int k, T v) { return fabs(double(d.dy[k]) * double(v)); });
+    const double b2 = tile_row_sum<G, double>(d.At.rp, d.At.ci, d.At.val, tile, d.n, [&](int k, T v) {
+      const double bb = double(d.dy[k]) * double(v);
       return d.sig[k] * bb * bb;
     });
-    if (valid && it.lane_g == 0) {
-      const double mw = h1 + fmax(b1, sqrt(b2));
+    const long long i = tile + ti.lane;
+    if (i < d.n) {
+      const double ei = double(d.ex[i]);
+      const double mw = h1 * ei + fmax(b1 * ei, sqrt(b2) * ei);
       mwx[i] = mw;
       d.taux[i] = T(ei * ei * (0.99 / mw));
+      d.itaux[i] = T(mw / (0.99 * ei * ei));
     }
   }
 }
@@ -602,30 +603,32 @@ __global__ void __launch_bounds__(kBlock) k_mw_cols(Dev<T> d, double *mwx) {
 // eta_eff / (kappa omega) = d^2 * 0.99 / m_y.
 template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_my_rows(Dev<T> d, const double *mwx) {
-  GroupIter<G> it;
-  for (long long base = it.first; base < d.m; base += it.step) {
-    const long long j = base + it.sub;
-    const bool valid = j < d.m;
-    const double dj = valid ? double(d.dy[j]) : 0.0;
-    const double a = row_sum<G, double>(d.A.rp, d.A.ci, d.A.val, j, valid, it.lane_g, [&](int k, T v) {
-      const double bb = dj * double(v) * double(d.ex[k]);
+  TileIter ti;
+  for (long long tile = ti.first; tile < d.m; tile += ti.step) {
+    const double a = tile_row_sum<G, double>(d.A.rp, d.A.ci, d.A.val, tile, d.m, [&](int k, T v) {
+      const double bb = double(v) * double(d.ex[k]);
       return bb * bb / mwx[k];
     });
-    if (valid && it.lane_g == 0) {
+    const long long j = tile + ti.lane;
+    if (j < d.m) {
+      const double dj = double(d.dy[j]);
       const double sg = d.sig[j];
       const double er = double(d.er[j]);
       const double br = dj * er;
       const double mwr = er * er * sg + br;
       d.taur[j] = T(er * er * (0.99 / mwr));
-      double my = a + br * br / mwr;
+      d.itaur[j] = T(mwr / (0.99 * er * er));
+      double my = a * dj * dj + br * br / mwr;
       if (j >= d.mE) {
         const double es = double(d.es[j]);
         const double bs = dj * es;
         const double mws = fmax(bs, sqrt(sg * bs * bs));
         d.taus[j] = T(es * es * (0.99 / mws));
+        d.itaus[j] = T(mws / (0.99 * es * es));
         my += bs * bs / mws;
       }
       d.eta[j] = T(dj * dj * (0.99 / my));
+      d.ieta[j] = T(my / (0.99 * dj * dj));
     }
   }
 }
@@ -636,13 +639,12 @@ __global__ void __launch_bounds__(kBlock) k_cache_cols(Dev<T> d) {
   const int cur = d.st->cur;
   const T *__restrict__ x = d.x[cur];
   const T *__restrict__ y = d.y[cur];
-  GroupIter<G> it;
-  for (long long base = it.first; base < d.n; base += it.step) {
-    const long long i = base + it.sub;
-    const bool valid = i < d.n;
-    const T hx = row_sum<G, T>(d.H.rp, d.H.ci, d.H.val, i, valid, it.lane_g, [&](int k, T a) { return a * x[k]; });
-    const T aty = row_sum<G, T>(d.At.rp, d.At.ci, d.At.val, i, valid, it.lane_g, [&](int k, T a) { return a * y[k]; });
-    if (valid && it.lane_g == 0) {
+  TileIter ti;
+  for (long long tile = ti.first; tile < d.n; tile += ti.step) {
+    const T hx = tile_row_sum<G, T>(d.H.rp, d.H.ci, d.H.val, tile, d.n, [&](int k, T a) { return a * x[k]; });
+    const T aty = tile_row_sum<G, T>(d.At.rp, d.At.ci, d.At.val, tile, d.n, [&](int k, T a) { return a * y[k]; });
+    const long long i = tile + ti.lane;
+    if (i < d.n) {
       d.Hx[cur][i] = hx;
       d.Aty[cur][i] = aty;
     }
@@ -676,7 +678,7 @@ __global__ void __launch_bounds__(kRedThreads) k_inner_begin(DevState *st, const
   final_reduce<16>(part + P_CK_R * kMaxBlocks, nb_r, CK_MAXMASK, a);
   final_reduce<16>(part + P_CK_C * kMaxBlocks, nb_c, CK_MAXMASK, b);
   if (threadIdx.x != 0) return;
-  const double om = st->omega;
+  const double om = st->omega;  // restart metric of the inner start
   st->k_restart = sqrt(om * (a[4] + b[4]) + (a[5] + b[5]) / om);
   st->k_last = INFINITY;
   st->status = ST_RUNNING;

@@ -304,13 +304,12 @@ __global__ void __launch_bounds__(kBlock) k_outer_rows(Dev<T> d, Mat<double> Ad,
   double q[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) q[k] = 0.0;
-  GroupIter<G> it;
-  for (long long base = it.first; base < d.m; base += it.step) {
-    const long long j = base + it.sub;
-    const bool valid = j < d.m;
-    const double ax = row_sum<G, double>(Ad.rp, Ad.ci, Ad.val, j, valid, it.lane_g,
-                                         [&](int k, double a) { return a * double(x[k]); });
-    if (valid && it.lane_g == 0) {
+  TileIter ti;
+  for (long long tile = ti.first; tile < d.m; tile += ti.step) {
+    const double ax = tile_row_sum<G, double>(Ad.rp, Ad.ci, Ad.val, tile, d.m,
+                                              [&](int k, double a) { return a * double(x[k]); });
+    const long long j = tile + ti.lane;
+    if (j < d.m) {
       const double lo = lc[j], hi = uc[j];
       if (update) {
         double s;
@@ -334,10 +333,7 @@ __global__ void __launch_bounds__(kBlock) k_outer_rows(Dev<T> d, Mat<double> Ad,
       q[1] = fmax(q[1], spv);
       const double dc = Dc[j];
       q[2] = fmax(q[2], viol / dc);
-      double spu = fabs(ax) / dc;
-      if (isfinite(lo)) spu = fmax(spu, fabs(lo) / dc);
-      if (isfinite(hi)) spu = fmax(spu, fabs(hi) / dc);
-      q[3] = fmax(q[3], spu);
+      q[3] = fmax(q[3], spv / dc);
     }
   }
   block_reduce_store<12>(q, OUT_MAXMASK, d.part);
@@ -353,15 +349,14 @@ __global__ void __launch_bounds__(kBlock) k_outer_cols(Dev<T> d, Mat<double> Hd,
   double q[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) q[k] = 0.0;
-  GroupIter<G> it;
-  for (long long base = it.first; base < d.n; base += it.step) {
-    const long long i = base + it.sub;
-    const bool valid = i < d.n;
-    const double hx = row_sum<G, double>(Hd.rp, Hd.ci, Hd.val, i, valid, it.lane_g,
-                                         [&](int k, double a) { return a * double(x[k]); });
-    const double atl = row_sum<G, double>(Atd.rp, Atd.ci, Atd.val, i, valid, it.lane_g,
-                                          [&](int k, double a) { return a * lam[k]; });
-    if (valid && it.lane_g == 0) {
+  TileIter ti;
+  for (long long tile = ti.first; tile < d.n; tile += ti.step) {
+    const double hx = tile_row_sum<G, double>(Hd.rp, Hd.ci, Hd.val, tile, d.n,
+                                              [&](int k, double a) { return a * double(x[k]); });
+    const double atl = tile_row_sum<G, double>(Atd.rp, Atd.ci, Atd.val, tile, d.n,
+                                               [&](int k, double a) { return a * lam[k]; });
+    const long long i = tile + ti.lane;
+    if (i < d.n) {
       const double xi = double(x[i]);
       const double qx = hx - ginv * xi;
       const double g = qx + c[i] + atl;
@@ -387,14 +382,14 @@ __global__ void __launch_bounds__(kBlock) k_outer_cols(Dev<T> d, Mat<double> Hd,
   block_reduce_store<12>(q, OUT_MAXMASK, d.part + 12 * kMaxBlocks);
 }
 
-// Eq. penalty-trigger-eq with the growth rule; rows within the primal target
-// are left alone.  Also stores r as the previous residual.
+// Eq. penalty-trigger-eq with the growth rule (only when `grow`: the primal
+// part of the termination test still fails).  Stores r as the previous residual.
 __global__ void k_sigma_update(int m, int mE, double *sig, const double *lam, const double *rcur, double *rprev,
-                               double theta, double rtarget, double rn, double dsig, double smax) {
+                               double theta, int grow, double rn, double dsig, double smax) {
   PDNQP_GRID_STRIDE(j, m) {
     const double r = rcur[j];
     const bool active = j < mE || lam[j] != 0.0;
-    if (active && fabs(r) > theta * fabs(rprev[j]) && fabs(r) > rtarget && rn > 0.0)
+    if (grow && active && fabs(r) > theta * fabs(rprev[j]) && rn > 0.0)
       sig[j] = fmin(smax, sig[j] * fmax(1.0, dsig * fabs(r) / rn));
     rprev[j] = r;
   }

@@ -49,6 +49,7 @@ struct Params {
   double delta_sigma = 2.0, sigma_max = 1e6, tol_floor = 0.1;
   double gamma_override = 0.0;
   int chunk = 32;
+  long long iter_budget = 4000000000000000000LL;
   int g_rows = 0, g_cols = 0;  // lanes per CSR row (0 = from the mean row length)
 };
 
@@ -57,6 +58,7 @@ struct Result {
   double rp = 0, rd = 0, sp = 1, sd = 1, rel_kkt = 0;
   long long outer = 0, inner = 0, trials = 0, restarts = 0, passes = 0;
   double seconds = 0, obj = 0;
+  long long launches = 0;
 };
 
 class SolverBase {

@@ -212,8 +212,8 @@ class Solver : public SolverBase {
     Hd_ = {n_, qrp, qci, qv_};
     Ad_ = {m_, arp, aci, av_};
     Atd_ = {n_, atrp, atci, atv_};
-    gA_ = prm.g_rows ? prm.g_rows : pick_g(nnzA_, m_);
-    gN_ = prm.g_cols ? prm.g_cols : pick_g(std::max(nnzH_, nnzA_), n_);
+    gA0_ = gA_ = prm.g_rows ? prm.g_rows : pick_g(nnzA_, m_);
+    gN0_ = gN_ = prm.g_cols ? prm.g_cols : pick_g(std::max(nnzH_, nnzA_), n_);
     // FP64 vectors.
     PDNQP_TRY(upload(&c_, P.c));
     PDNQP_TRY(upload(&lxd_, P.lx));
@@ -420,9 +420,10 @@ class Solver : public SolverBase {
       PDNQP_CK(cudaMemsetAsync(d.s[b], 0, sizeof(T) * std::max(m_, 1), s_));
       PDNQP_CK(cudaMemsetAsync(d.sbar[b], 0, sizeof(T) * std::max(m_, 1), s_));
     }
-    T **nv[] = {&d.qx, &d.lx, &d.ux, &d.taux, &d.ex, &d.xst, &d.Atybar};
+    T **nv[] = {&d.qx, &d.lx, &d.ux, &d.taux, &d.itaux, &d.ex, &d.xst, &d.Atybar};
     for (T **p : nv) PDNQP_TRY(dalloc(p, n_));
-    T **mv[] = {&d.eta, &d.taus, &d.taur, &d.es, &d.er, &d.dy, &d.h, &d.ls, &d.us, &d.yst, &d.sst, &d.rst, &d.Bwbar};
+    T **mv[] = {&d.eta, &d.taus, &d.taur, &d.ieta, &d.itaus, &d.itaur, &d.es, &d.er, &d.dy, &d.h,
+                 &d.ls, &d.us, &d.yst, &d.sst, &d.rst, &d.Bwbar};
     for (T **p : mv) {
       PDNQP_TRY(dalloc(p, m_));
       PDNQP_CK(cudaMemsetAsync(*p, 0, sizeof(T) * std::max(m_, 1), s_));
@@ -443,8 +444,9 @@ class Solver : public SolverBase {
   }
 
   // ------------------------------------------------------- launchers
-  int nb_rows() const { return grid_rows_g(std::max(m_, 1), gA_); }
-  int nb_cols() const { return grid_rows_g(n_, gN_); }
+  // Tile kernels: one warp per 32 rows and trip, kBlock / 32 warps per block.
+  int nb_rows() const { return grid_for(std::max(m_, 1), kBlock); }
+  int nb_cols() const { return grid_for(n_, kBlock); }
   void launch_primal() { k_primal<T><<<grid_n(), kBlock, 0, s_>>>(d_); }
   void launch_rows() {
     with_G(gA_, [&](auto GG) { k_rows<T, decltype(GG)::value><<<nb_rows(), kBlock, 0, s_>>>(d_); });
@@ -452,6 +454,7 @@ class Solver : public SolverBase {
   void launch_cols() {
     with_G(gN_, [&](auto GG) { k_cols<T, decltype(GG)::value><<<nb_cols(), kBlock, 0, s_>>>(d_); });
   }
+  static constexpr int kSlotKernels = 9;
   void launch_slot() {
     launch_primal();
     launch_rows();
@@ -467,8 +470,16 @@ class Solver : public SolverBase {
     with_G(gN_, [&](auto GG) { k_check_cols<T, decltype(GG)::value><<<nb_cols(), kBlock, 0, s_>>>(d_, mode); });
   }
 
+  // Lanes per CSR row: parameter override, else the mean-row-length choice of setup.
+  void apply_g(const Params &prm) {
+    gA_ = prm.g_rows > 0 ? prm.g_rows : gA0_;
+    gN_ = prm.g_cols > 0 ? prm.g_cols : gN0_;
+  }
+
   int build_graph(int chunk) {
-    if (gexec_ && chunk == graph_chunk_) return 0;
+    if (gexec_ && chunk == graph_chunk_ && gA_ == graph_gA_ && gN_ == graph_gN_) return 0;
+    graph_gA_ = gA_;
+    graph_gN_ = gN_;
     if (gexec_) {
       cudaGraphExecDestroy(gexec_);
       gexec_ = nullptr;
@@ -585,6 +596,7 @@ class Solver : public SolverBase {
     PDNQP_CK(cudaMemcpyAsync(st_, &S, sizeof(S), cudaMemcpyHostToDevice, s_));
     launch_check(1);
     k_inner_begin<<<1, kRedThreads, 0, s_>>>(st_, part_, nb_rows(), nb_cols());
+    launches_ += 9 + 3LL * prm.ruiz_inner;
     PDNQP_CK(cudaGetLastError());
     return 0;
   }
@@ -601,6 +613,7 @@ class Solver : public SolverBase {
     PDNQP_TRY(build_graph(prm.chunk));
     for (;;) {
       PDNQP_CK(cudaGraphLaunch(gexec_, s_));
+      launches_ += (long long)prm.chunk * kSlotKernels;
       PDNQP_TRY(read_state(S));
       if (S->status != ST_RUNNING) return 0;
       if (seconds_since(t0) > prm.time_limit) return 1;
@@ -638,6 +651,7 @@ class Solver : public SolverBase {
   // Outer residuals; update = 1 also applies the multiplier update first.
   int outer_residuals(int update, double *q) {
     const double ginv = 1.0 / gamma_;
+    launches_ += 4;
     double a[12] = {0}, b[12] = {0};
     if (m_) {
       const int nb = nb_rows();
@@ -667,6 +681,8 @@ class Solver : public SolverBase {
       PDNQP_TRY(regamma(gamma_pending_));
       gamma_pending_ = 0;
     }
+    launches_ = 0;
+    apply_g(prm);
     PDNQP_TRY(start_point(prm));
     double dta = 1.0, dtr = 1.0, eak = 1.0, erk = 1.0;
     int status = PDNQP_ITER_LIMIT;
@@ -677,7 +693,12 @@ class Solver : public SolverBase {
         status = PDNQP_TIME_LIMIT;
         break;
       }
-      PDNQP_TRY(inner_setup(prm, dta, dtr, prm.k_in, -1, 0));
+      const long long left = prm.iter_budget - accepted_;
+      if (left <= 0) {
+        status = PDNQP_ITER_LIMIT;
+        break;
+      }
+      PDNQP_TRY(inner_setup(prm, dta, dtr, std::min(prm.k_in, left), -1, 0));
       DevState S;
       int tl = 0;
       PDNQP_TRY(tl = run_until_stop(prm, &S, t0));
@@ -700,16 +721,17 @@ class Solver : public SolverBase {
       PDNQP_TRY(outer_residuals(1, q));
       const double rps = q[0], sps = std::max(1.0, q[1]), rpu = q[2], spu = std::max(1.0, q[3]), rn = q[4];
       const double rds = q[5], rdu = q[7], sdu = std::max(1.0, q[8]), dxz = q[9];
-      (void)rps;
       if (rpu <= ea + er * spu && rdu <= ea + er * sdu) {
         status = PDNQP_SOLVED;
         ++k;
         break;
       }
-      // Eq. penalty-trigger-eq.
+      // Eq. penalty-trigger-eq; penalties grow only while the primal part of
+      // Eq. outer-termination fails (scaled or original data).
+      const int grow = !(rpu <= ea + er * spu && rps <= ea + er * sps);
       if (m_)
-        k_sigma_update<<<grid_m(), kBlock, 0, s_>>>(m_, mE_, sig_, lam_, rcur_, rprev_, prm.theta_sigma,
-                                                    ea + er * sps, rn, prm.delta_sigma, prm.sigma_max);
+        k_sigma_update<<<grid_m(), kBlock, 0, s_>>>(m_, mE_, sig_, lam_, rcur_, rprev_, prm.theta_sigma, grow, rn,
+                                                    prm.delta_sigma, prm.sigma_max);
       // Eq. inner-tolerance-factor.
       const double ratio = rds > 0.0 ? std::min(1.0, (dxz / gamma_) / rds) : 1.0;
       const double rho = prm.rho_in_max - (prm.rho_in_max - prm.rho_in_min) * ratio;
@@ -718,8 +740,8 @@ class Solver : public SolverBase {
       // Eq. center-update / center-tolerance-update.
       if (rps <= eak + erk * sps) {
         k_copy_to_double<T><<<grid_n(), kBlock, 0, s_>>>(z_, d_.x[0], n_);
-        eak *= prm.rho_z;
-        erk *= prm.rho_z;
+        eak = std::max(eak * prm.rho_z, ea);
+        erk = std::max(erk * prm.rho_z, er);
       }
       PDNQP_CK(cudaGetLastError());
     }
@@ -741,6 +763,7 @@ class Solver : public SolverBase {
     res_.restarts = restarts_;
     res_.passes = 3 * trials_ + 2 * (accepted_ / std::max(1, prm.k_chk));
     res_.seconds = seconds_since(t0);
+    res_.launches = launches_;
     solved_once_ = true;
     return status;
   }
@@ -793,6 +816,7 @@ class Solver : public SolverBase {
       PDNQP_TRY(regamma(gamma_pending_));
       gamma_pending_ = 0;
     }
+    apply_g(prm);
     PDNQP_TRY(start_point(prm));
     const long long len = 2 * ((long long)n_ + (m_ - mE_) + m_ + m_) + 8;
     int got = 0;
@@ -822,7 +846,7 @@ class Solver : public SolverBase {
   std::vector<void *> allocs_;
   int n_ = 0, m_ = 0, mE_ = 0;
   long long nnzA_ = 0, nnzH_ = 0;
-  int gA_ = 8, gN_ = 8;
+  int gA_ = 8, gN_ = 8, gA0_ = 8, gN0_ = 8, graph_gA_ = 0, graph_gN_ = 0;
   Mat<double> Hd_{}, Ad_{}, Atd_{};
   double *qv_ = nullptr, *av_ = nullptr, *atv_ = nullptr;
   int *qdiag_ = nullptr;
@@ -839,7 +863,7 @@ class Solver : public SolverBase {
   int graph_chunk_ = 0;
   double cs_ = 1.0, qnorm_ = 0.0, gamma_ = 1.0, lam_min_ = 0.0, sigma0_ = 1.0, omega_ = 1.0;
   double gamma_pending_ = 0.0;
-  long long trials_ = 0, accepted_ = 0, restarts_ = 0;
+  long long trials_ = 0, accepted_ = 0, restarts_ = 0, launches_ = 0;
   bool ready_ = false, solved_once_ = false, has_x0_ = false, has_l0_ = false, own_stream_ = false;
   std::vector<double> h_x0_, h_l0_;
   Result res_;

@@ -184,16 +184,24 @@ def mid_qp(seed: int = 0, n: int = 50_000, m: int = 25_000, q_mean: float = 8.0,
     n_free = int(round(free_frac * n))
     free = rng.choice(n, size=n_free, replace=False)
     l_x[free], u_x[free] = -np.inf, np.inf
-    # Every free variable must appear in at least two constraint rows so that the
-    # feasible set stays bounded along it.
+    # Keep the feasible set bounded along the free variables: n_free distinct
+    # "pivot" rows each hold exactly one free variable (coefficient of magnitude
+    # in [0.5, 1.5]) and no other free variable, so that every free variable is
+    # confined by its pivot row's two-sided bounds given the boxed variables.
+    is_free = np.zeros(n, dtype=bool)
+    is_free[free] = True
+    pivots = rng.choice(m, size=n_free, replace=False)
     Acoo = A.tocoo()
-    colcnt = np.bincount(Acoo.col, minlength=n)
-    need = free[colcnt[free] < 2]
-    if need.size:
-        extra_r = rng.integers(0, m, size=2 * need.size)
-        extra_c = np.repeat(need, 2)
-        A = (A + sp.coo_matrix((rng.standard_normal(extra_r.size), (extra_r, extra_c)), shape=(m, n))).tocsr()
-        A.sum_duplicates()
+    drop = np.isin(Acoo.row, pivots) & is_free[Acoo.col]
+    pr = pivots
+    pc = rng.permutation(free)
+    pv = rng.choice([-1.0, 1.0], size=n_free) * rng.uniform(0.5, 1.5, size=n_free)
+    keep = ~drop
+    rows = np.concatenate([Acoo.row[keep], pr])
+    cols = np.concatenate([Acoo.col[keep], pc])
+    vals = np.concatenate([Acoo.data[keep], pv])
+    A = sp.coo_matrix((vals, (rows, cols)), shape=(m, n)).tocsr()
+    A.sum_duplicates()
     c = rng.standard_normal(n)
     x0 = rng.uniform(0.0, 1.0, size=n)
     x0[free] = rng.uniform(-1.0, 1.0, size=n_free)
