@@ -94,6 +94,8 @@ typedef struct {
   double lambda_min;         /* Lanczos estimate of lambda_min of the scaled Q */
   double obj;                /* c'x + 1/2 x'Qx at the returned x */
   int64_t kernel_launches;   /* CUDA kernels launched by the last pdnqp_solve (graph nodes included) */
+  double inner_seconds;      /* wall time spent in the device-driven inner loops (Algorithm 4 iterations) */
+  double setup_seconds;      /* wall time of the per-outer-iteration inner setup (warm start, scaling, steps) */
 } pdnqp_residuals;
 
 /* Creation options (pdnqp_create uses precision = PDNQP_FP64, device = current,

@@ -332,6 +332,8 @@ int pdnqp_get(const pdnqp_t *h, double *x, double *y, pdnqp_residuals *r) {
     r->lambda_min = h->solver->lambda_min();
     r->obj = R.obj;
     r->kernel_launches = R.launches;
+    r->inner_seconds = R.inner_seconds;
+    r->setup_seconds = R.setup_seconds;
   }
   return 0;
 }
@@ -358,8 +360,8 @@ int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0) {
   X(ruiz_inner, i, 0.0, 1000.0) X(lanczos_steps, i, 1.0, 100000.0) X(k_chk, i, 1.0, 1e9)           \
   X(beta_suff, d, 0.0, 1.0) X(beta_nec, d, 0.0, 1.0) X(beta_art, d, 0.0, 1.0)                      \
   X(rej_limit, i, 1.0, 1e9) X(kappa_shrink, d, 1e-6, 0.999999) X(delta_sigma, d, 1.0, 1e300)       \
-  X(sigma_max, d, 1e-300, 1e300) X(tol_floor, d, 0.0, 1.0) X(chunk, i, 1.0, 4096.0)               \
-  X(g_rows, i, 0.0, 32.0) X(g_cols, i, 0.0, 32.0) X(iter_budget, ll, 1.0, 4e18)
+  X(sigma_max, d, 1e-300, 1e300) X(tol_floor, d, 0.0, 1.0) X(chunk, i, 1.0, 65536.0)               \
+  X(g_rows, i, 0.0, 16.0) X(g_cols, i, 0.0, 16.0) X(iter_budget, ll, 1.0, 4e18)
 
 int pdnqp_set_param(pdnqp_t *h, const char *name, double value) {
   if (!h || !name) return fail(h, PDNQP_ERR_ARG, "NULL handle or name");

@@ -44,6 +44,7 @@ struct DevState {
   long long pause_at;  // debug: pause after this many accepted steps (-1: never)
   long long k_chk;     // check period
   long long rej_limit;
+  long long slot_left; // trials left in the current graph launch (bounds each device loop)
   double kappa;        // common step factor of the rejection rule
   double omega;        // primal weight (Eq. primal-weight-update)
   double alpha_acc;    // alpha of the last accepted trial
@@ -192,62 +193,63 @@ __device__ __forceinline__ Acc shfl_any(Acc v, int src) {
   return __shfl_sync(0xffffffffu, v, src);
 }
 
-// Lane l of the warp returns sum_{k in row(tile + l)} f(col_k, val_k) (0 past
-// nrows).  rp is read once per tile (coalesced) and distributed by shuffles.
-template <int G, typename Acc, typename T, typename F>
-__device__ __forceinline__ Acc tile_row_sum(const int *__restrict__ rp, const int *__restrict__ ci,
-                                            const T *__restrict__ val, long long tile, long long nrows, F f) {
-  constexpr int RPP = 32 / G;  // rows per pass
-  const int lane = threadIdx.x & 31;
-  const int gid = lane / G, lg = lane & (G - 1);
-  const long long my = tile + lane;
-  int rb = 0, re = 0;
-  if (my < nrows) {
-    rb = rp[my];
-    re = rp[my + 1];
-  }
-  Acc mine = Acc(0);
-#pragma unroll
-  for (int pass = 0; pass < G; ++pass) {
-    const int owner = pass * RPP + gid;  // lane that owns the row this group works on
-    const int b = __shfl_sync(0xffffffffu, rb, owner);
-    const int e = __shfl_sync(0xffffffffu, re, owner);
-    Acc a = Acc(0);
-    for (int k = b + lg; k < e; k += G) a += f(ci[k], val[k]);
-    a = group_sum<G, Acc>(a);
-    const int src = (lane - pass * RPP) * G;
-    const Acc v = shfl_any<Acc>(a, src & 31);
-    if (lane >= pass * RPP && lane < (pass + 1) * RPP) mine = v;
-  }
-  return mine;
+// Per-warp staging buffer of one CSR-stream chunk: 32 * K entries.
+template <int K, typename Acc>
+__device__ __forceinline__ Acc *warp_stage_buffer() {
+  __shared__ Acc buf[kBlock / 32][32 * K];
+  return buf[threadIdx.x >> 5];
 }
 
-template <int G, typename Acc, typename T, typename F>
-__device__ __forceinline__ Acc tile_row_max(const int *__restrict__ rp, const int *__restrict__ ci,
-                                            const T *__restrict__ val, long long tile, long long nrows, F f) {
-  constexpr int RPP = 32 / G;
+// CSR-stream row reduction over a warp tile of 32 consecutive rows: the
+// tile's contiguous nonzero range is streamed in chunks of 32 * K entries;
+// each lane loads K entries with coalesced, independent loads, evaluates
+// f(col, val) (including its gather) and stores it in the warp's staging
+// buffer; then lane l reduces the slice of the chunk that belongs to row
+// tile + l.  Rows of any length are handled (a long row spans several
+// chunks).  Lane l returns the result of row tile + l (0 past nrows).
+template <int K, bool IsMax, typename Acc, typename T, typename F>
+__device__ __forceinline__ Acc tile_stream(const int *__restrict__ rp, const int *__restrict__ ci,
+                                           const T *__restrict__ val, long long tile, long long nrows, F f) {
   const int lane = threadIdx.x & 31;
-  const int gid = lane / G, lg = lane & (G - 1);
+  Acc *sb = warp_stage_buffer<K, Acc>();
   const long long my = tile + lane;
+  const long long last = (nrows - 1 - tile) < 31 ? (nrows - 1 - tile) : 31;  // last valid lane (>= 0)
   int rb = 0, re = 0;
   if (my < nrows) {
     rb = rp[my];
     re = rp[my + 1];
   }
-  Acc mine = Acc(0);
+  const int base = __shfl_sync(0xffffffffu, rb, 0);
+  const int end = __shfl_sync(0xffffffffu, re, (int)last);
+  if (my >= nrows) rb = re = end;
+  Acc acc = Acc(0);
+  for (int c0 = base; c0 < end; c0 += 32 * K) {
+    Acc p[K];
 #pragma unroll
-  for (int pass = 0; pass < G; ++pass) {
-    const int owner = pass * RPP + gid;
-    const int b = __shfl_sync(0xffffffffu, rb, owner);
-    const int e = __shfl_sync(0xffffffffu, re, owner);
-    Acc a = Acc(0);
-    for (int k = b + lg; k < e; k += G) a = fmax(a, f(ci[k], val[k]));
-    a = group_max<G, Acc>(a);
-    const int src = (lane - pass * RPP) * G;
-    const Acc v = shfl_any<Acc>(a, src & 31);
-    if (lane >= pass * RPP && lane < (pass + 1) * RPP) mine = v;
+    for (int j = 0; j < K; ++j) {
+      const int k = c0 + j * 32 + lane;
+      p[j] = k < end ? f(ci[k], val[k]) : Acc(0);
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) sb[j * 32 + lane] = p[j];
+    __syncwarp();
+    const int lo = rb > c0 ? rb : c0;
+    const int hi = re < c0 + 32 * K ? re : c0 + 32 * K;
+    for (int k = lo; k < hi; ++k) acc = IsMax ? fmax(acc, sb[k - c0]) : acc + sb[k - c0];
+    __syncwarp();
   }
-  return mine;
+  return acc;
+}
+
+template <int K, typename Acc, typename T, typename F>
+__device__ __forceinline__ Acc tile_row_sum(const int *__restrict__ rp, const int *__restrict__ ci,
+                                            const T *__restrict__ val, long long tile, long long nrows, F f) {
+  return tile_stream<K, false, Acc>(rp, ci, val, tile, nrows, f);
+}
+template <int K, typename Acc, typename T, typename F>
+__device__ __forceinline__ Acc tile_row_max(const int *__restrict__ rp, const int *__restrict__ ci,
+                                            const T *__restrict__ val, long long tile, long long nrows, F f) {
+  return tile_stream<K, true, Acc>(rp, ci, val, tile, nrows, f);
 }
 
 inline int grid_for(long long work_items, int per_block) {

@@ -86,19 +86,30 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_primal(Dev<T> d) {
   const DevState *st = d.st;
   if (st->status != ST_RUNNING) return;
-  const int cur = st->cur, ab = st->acur ^ st->accepted;
+  const int cur = st->cur, a0 = st->acur, acc = st->accepted;
   const double t = (double)st->t;
   const T alpha = T(2.0 / (t + 2.0));
   const T oma = T(1) - alpha;
   const T sc = T(st->kappa / st->omega);
+  const T ap = T(st->alpha_acc), omap = T(1) - ap;
   const T *__restrict__ x = d.x[cur];
   const T *__restrict__ Hx = d.Hx[cur];
   const T *__restrict__ Aty = d.Aty[cur];
-  const T *__restrict__ Hxb = d.Hxbar[ab];
   T *__restrict__ xt = d.x[1 - cur];
   PDNQP_GRID_STRIDE(i, d.n) {
-    const T g = d.qx[i] + oma * Hxb[i] + alpha * Hx[i] - Aty[i];
-    xt[i] = clampv<T>(x[i] - (sc * d.taux[i]) * g, d.lx[i], d.ux[i]);
+    const T xi = x[i], hxi = Hx[i];
+    T hxb;
+    if (acc) {
+      // Running averages of the previous acceptance (Algorithm 4), written to
+      // the other buffer: wbar <- (1 - alpha) wbar + alpha w.
+      hxb = omap * d.Hxbar[a0][i] + ap * hxi;
+      d.Hxbar[a0 ^ 1][i] = hxb;
+      d.xbar[a0 ^ 1][i] = omap * d.xbar[a0][i] + ap * xi;
+    } else {
+      hxb = d.Hxbar[a0][i];
+    }
+    const T g = d.qx[i] + oma * hxb + alpha * hxi - Aty[i];
+    xt[i] = clampv<T>(xi - (sc * d.taux[i]) * g, d.lx[i], d.ux[i]);
   }
 }
 
@@ -112,11 +123,12 @@ template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_rows(Dev<T> d) {
   const DevState *st = d.st;
   if (st->status != ST_RUNNING) return;
-  const int cur = st->cur, nx = 1 - cur, ab = st->acur ^ st->accepted;
+  const int cur = st->cur, nx = 1 - cur, a0 = st->acur, acc = st->accepted;
   const double t = (double)st->t;
   const T alpha = T(2.0 / (t + 2.0)), oma = T(1) - alpha;
   const T beta = T(t / (t + 1.0));
   const T sct = T(st->kappa / st->omega), sce = T(st->kappa * st->omega);
+  const T ap = T(st->alpha_acc), omap = T(1) - ap;
   const T *__restrict__ xt = d.x[nx];
   T Lt = T(0), Le = T(0), RH = T(0), RB = T(0);
   TileIter ti;
@@ -124,7 +136,16 @@ __global__ void __launch_bounds__(kBlock) k_rows(Dev<T> d) {
     const T ax = tile_row_sum<G, T>(d.A.rp, d.A.ci, d.A.val, tile, d.m, [&](int k, T a) { return a * xt[k]; });
     const long long j = tile + ti.lane;
     if (j < d.m) {
-      const T y = d.y[cur][j], r = d.r[cur][j], rb = d.rbar[ab][j];
+      const T y = d.y[cur][j], r = d.r[cur][j];
+      T rb;
+      if (acc) {  // running averages of the previous acceptance
+        rb = omap * d.rbar[a0][j] + ap * r;
+        d.rbar[a0 ^ 1][j] = rb;
+        d.ybar[a0 ^ 1][j] = omap * d.ybar[a0][j] + ap * y;
+        if (j >= d.mE) d.sbar[a0 ^ 1][j] = omap * d.sbar[a0][j] + ap * d.s[cur][j];
+      } else {
+        rb = d.rbar[a0][j];
+      }
       const T lam = T(d.lam[j]), sig = T(d.sig[j]);
       const T rt = r - (sct * d.taur[j]) * (lam + sig * (oma * rb + alpha * r) + y);
       T bwt = ax - rt, ds = T(0);
@@ -185,46 +206,81 @@ __global__ void __launch_bounds__(kBlock) k_cols(Dev<T> d) {
 // Acceptance decision (single block, deterministic order).  On acceptance the
 // trial buffers become current (index flip); on rejection both step vectors
 // are shrunk through kappa.
-__global__ void __launch_bounds__(kRedThreads) k_decide(DevState *st, const double *part, int nb_r, int nb_c) {
-  if (st->status != ST_RUNNING) return;
+// The single-block kernels work on a shared-memory copy of the device state
+// (one coalesced load and store) instead of chains of dependent global
+// read-modify-writes.
+__device__ __forceinline__ void state_load(DevState &S, const DevState *g) {
+  for (int i = threadIdx.x; i < (int)(sizeof(DevState) / 4); i += blockDim.x) ((int *)&S)[i] = ((const int *)g)[i];
+  __syncthreads();
+}
+__device__ __forceinline__ void state_store(DevState *g, const DevState &S) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < (int)(sizeof(DevState) / 4); i += blockDim.x) ((int *)g)[i] = ((const int *)&S)[i];
+}
+
+// Start of one graph launch: at most `chunk` trials before control returns to
+// the host.
+__global__ void k_loop_begin(DevState *st, long long chunk) { st->slot_left = chunk; }
+
+// hw / hc: conditional handles of the device loop (WHILE over trial slots) and
+// of the periodic check (IF); 0 when the graph has no conditional nodes.
+__global__ void __launch_bounds__(kRedThreads) k_decide(DevState *stg, const double *part, int nb_r, int nb_c,
+                                                        cudaGraphConditionalHandle hw,
+                                                        cudaGraphConditionalHandle hc) {
+  __shared__ DevState S;
+  state_load(S, stg);
+  if (S.status != ST_RUNNING) {
+    if (threadIdx.x == 0) {
+      if (hw) cudaGraphSetConditional(hw, 0);
+      if (hc) cudaGraphSetConditional(hc, 0);
+    }
+    return;
+  }
   double a[4], b[4];
   final_reduce<4>(part + P_TR_R * kMaxBlocks, nb_r, 0u, a);
   final_reduce<4>(part + P_TR_C * kMaxBlocks, nb_c, 0u, b);
-  if (threadIdx.x != 0) return;
-  // Commit the averages computed after the previous acceptance.
-  st->acur ^= st->accepted;
-  st->accepted = 0;
-  st->restart_flag = 0;
-  st->check_due = 0;
-  st->trials += 1;
-  const double om = st->omega, ka = st->kappa;
-  const double lhs = (om / ka) * (a[0] + b[0]) + (a[1] + b[1]) / (ka * om);
-  const double rh = a[2] + b[2], rb = a[3] + b[3];
-  if (!isfinite(lhs) || !isfinite(rh) || !isfinite(rb)) {
-    st->status = ST_NUMERICAL_ERROR;
-    return;
+  if (threadIdx.x == 0) {
+    DevState *st = &S;
+    // Commit the averages materialised by this slot's primal / row kernels.
+    st->acur ^= st->accepted;
+    st->accepted = 0;
+    st->restart_flag = 0;
+    st->check_due = 0;
+    st->trials += 1;
+    const double om = st->omega, ka = st->kappa;
+    const double lhs = (om / ka) * (a[0] + b[0]) + (a[1] + b[1]) / (ka * om);
+    const double rh = a[2] + b[2], rb = a[3] + b[3];
+    if (!isfinite(lhs) || !isfinite(rh) || !isfinite(rb)) {
+      st->status = ST_NUMERICAL_ERROR;
+    } else if (0.5 * lhs >= 0.5 * rh + rb) {
+      st->alpha_acc = 2.0 / ((double)st->t + 2.0);
+      st->cur ^= 1;
+      st->accepted = 1;
+      st->t += 1;
+      st->t_total += 1;
+      st->accepted_all += 1;
+      st->rej = 0;
+      const bool due = (st->k_chk > 0 && st->t_total % st->k_chk == 0) || st->t_total == st->k_in;
+      st->check_due = due ? 1 : 0;
+      if (!due && st->t_total == st->pause_at) st->status = ST_PAUSED;
+    } else {
+      st->kappa *= st->shrink;
+      st->rej += 1;
+      if (st->rej >= st->rej_limit) st->status = ST_NUMERICAL_ERROR;
+    }
+    st->slot_left -= 1;
+    const bool run = st->status == ST_RUNNING;
+    if (hw) cudaGraphSetConditional(hw, (run && st->slot_left > 0) ? 1u : 0u);
+    if (hc) cudaGraphSetConditional(hc, (run && st->check_due) ? 1u : 0u);
   }
-  if (0.5 * lhs >= 0.5 * rh + rb) {
-    st->alpha_acc = 2.0 / ((double)st->t + 2.0);
-    st->cur ^= 1;
-    st->accepted = 1;
-    st->t += 1;
-    st->t_total += 1;
-    st->accepted_all += 1;
-    st->rej = 0;
-    const bool due = (st->k_chk > 0 && st->t_total % st->k_chk == 0) || st->t_total == st->k_in;
-    st->check_due = due ? 1 : 0;
-    if (!due && st->t_total == st->pause_at) st->status = ST_PAUSED;
-  } else {
-    st->kappa *= st->shrink;
-    st->rej += 1;
-    if (st->rej >= st->rej_limit) st->status = ST_NUMERICAL_ERROR;
-  }
+  state_store(stg, S);
 }
 
-// Running averages after an acceptance: bar[acur^1] = (1 - alpha) bar[acur]
-// + alpha w (Algorithm 4, "update the weighted averages"), for x, H x, s, r, y.
-// Reads and writes different buffers, so a repeated launch is harmless.
+// Materialises the running averages of a pending acceptance: bar[acur^1] =
+// (1 - alpha) bar[acur] + alpha w (Algorithm 4, "update the weighted
+// averages") for x, H x, s, r, y.  The trial kernels do this lazily; this
+// kernel is only used before the host reads a paused state.  Reads and writes
+// different buffers, so a repeated launch is harmless.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_average(Dev<T> d) {
   const DevState *st = d.st;
@@ -293,8 +349,12 @@ template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_check_rows(Dev<T> d, int mode) {
   const DevState *st = d.st;
   if (mode == 0 && !(st->status == ST_RUNNING && st->check_due)) return;
-  const int cur = st->cur, ab = st->acur ^ st->accepted;
-  const T *__restrict__ xb = d.xbar[ab];
+  // Averages of a pending acceptance are formed on the fly (and written for the
+  // row blocks); x bar is gathered as (1 - alpha) xbar + alpha x.
+  const int cur = st->cur, a0 = st->acur, acc = st->accepted, ab = a0 ^ acc;
+  const T ap = T(st->alpha_acc), omap = T(1) - ap;
+  const T *__restrict__ xb0 = d.xbar[a0];
+  const T *__restrict__ xc = d.x[cur];
   double q[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) q[k] = 0.0;
@@ -302,7 +362,9 @@ __global__ void __launch_bounds__(kBlock) k_check_rows(Dev<T> d, int mode) {
   for (long long tile = ti.first; tile < d.m; tile += ti.step) {
     T axb = T(0);
     if (mode == 0)
-      axb = tile_row_sum<G, T>(d.A.rp, d.A.ci, d.A.val, tile, d.m, [&](int k, T a) { return a * xb[k]; });
+      axb = tile_row_sum<G, T>(d.A.rp, d.A.ci, d.A.val, tile, d.m, [&](int k, T a) {
+        return a * (acc ? omap * xb0[k] + ap * xc[k] : xb0[k]);
+      });
     const long long j = tile + ti.lane;
     if (j < d.m) {
       const bool ineq = j >= d.mE;
@@ -314,11 +376,20 @@ __global__ void __launch_bounds__(kBlock) k_check_rows(Dev<T> d, int mode) {
       RowCand<T>::add(q, ineq, d.Bw[cur][j], h, sc, d.r[cur][j], d.y[cur][j], lam, sig, ls, us, es, er, dyv, sst,
                       rst, yst);
       if (mode == 0) {
-        const T sa = ineq ? d.sbar[ab][j] : T(0);
-        const T ra = d.rbar[ab][j];
+        T sa = ineq ? d.sbar[a0][j] : T(0), ra = d.rbar[a0][j], ya = d.ybar[a0][j];
+        if (acc) {
+          ra = omap * ra + ap * d.r[cur][j];
+          ya = omap * ya + ap * d.y[cur][j];
+          d.rbar[ab][j] = ra;
+          d.ybar[ab][j] = ya;
+          if (ineq) {
+            sa = omap * sa + ap * d.s[cur][j];
+            d.sbar[ab][j] = sa;
+          }
+        }
         const T bwa = axb - sa - ra;
         d.Bwbar[j] = bwa;
-        RowCand<T>::add(q + 8, ineq, bwa, h, sa, ra, d.ybar[ab][j], lam, sig, ls, us, es, er, dyv, sst, rst, yst);
+        RowCand<T>::add(q + 8, ineq, bwa, h, sa, ra, ya, lam, sig, ls, us, es, er, dyv, sst, rst, yst);
       }
     }
   }
@@ -348,7 +419,9 @@ template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_check_cols(Dev<T> d, int mode) {
   const DevState *st = d.st;
   if (mode == 0 && !(st->status == ST_RUNNING && st->check_due)) return;
-  const int cur = st->cur, ab = st->acur ^ st->accepted;
+  // y bar of a pending acceptance was materialised by k_check_rows.
+  const int cur = st->cur, a0 = st->acur, acc = st->accepted, ab = a0 ^ acc;
+  const T ap = T(st->alpha_acc), omap = T(1) - ap;
   const T *__restrict__ yb = d.ybar[ab];
   double q[16];
 #pragma unroll
@@ -364,7 +437,14 @@ __global__ void __launch_bounds__(kBlock) k_check_cols(Dev<T> d, int mode) {
       col_cand<T>(q, d.x[cur][i], d.Hx[cur][i], d.Aty[cur][i], qx, lx, ux, ex, xst);
       if (mode == 0) {
         d.Atybar[i] = atyb;
-        col_cand<T>(q + 8, d.xbar[ab][i], d.Hxbar[ab][i], atyb, qx, lx, ux, ex, xst);
+        T xa = d.xbar[a0][i], ha = d.Hxbar[a0][i];
+        if (acc) {
+          xa = omap * xa + ap * d.x[cur][i];
+          ha = omap * ha + ap * d.Hx[cur][i];
+          d.xbar[ab][i] = xa;
+          d.Hxbar[ab][i] = ha;
+        }
+        col_cand<T>(q + 8, xa, ha, atyb, qx, lx, ux, ex, xst);
       }
     }
   }
@@ -373,51 +453,63 @@ __global__ void __launch_bounds__(kBlock) k_check_cols(Dev<T> d, int mode) {
 
 // Decisions of the check (single block): inner termination of both candidates
 // (Eq. inner-termination), iteration limit, restart criteria and primal weight.
-__global__ void __launch_bounds__(kRedThreads) k_check_final(DevState *st, const double *part, int nb_r, int nb_c) {
-  if (!(st->status == ST_RUNNING && st->check_due)) return;
+__global__ void __launch_bounds__(kRedThreads) k_check_final(DevState *stg, const double *part, int nb_r, int nb_c,
+                                                             cudaGraphConditionalHandle hw) {
+  __shared__ DevState S;
+  state_load(S, stg);
+  if (!(S.status == ST_RUNNING && S.check_due)) return;
   double a[16], b[16];
   final_reduce<16>(part + P_CK_R * kMaxBlocks, nb_r, CK_MAXMASK, a);
   final_reduce<16>(part + P_CK_C * kMaxBlocks, nb_c, CK_MAXMASK, b);
-  if (threadIdx.x != 0) return;
-  double q[16];
-  for (int k = 0; k < 16; ++k) q[k] = ((CK_MAXMASK >> k) & 1u) ? fmax(a[k], b[k]) : a[k] + b[k];
-  for (int k = 0; k < 16; ++k) st->chk[k] = q[k];
-  // The averages computed after this trial's acceptance are committed here.
-  st->acur ^= st->accepted;
-  st->accepted = 0;
-  st->restart_flag = 0;
-  const double dta = st->dta, dtr = st->dtr;
-  const double spc = fmax(1.0, q[1]), sdc = fmax(1.0, q[3]);
-  const double spa = fmax(1.0, q[9]), sda = fmax(1.0, q[11]);
-  const bool okc = q[0] <= dta + dtr * spc && q[2] <= dta + dtr * sdc;
-  const bool oka = q[8] <= dta + dtr * spa && q[10] <= dta + dtr * sda;
-  if (!st->ignore_conv) {
-    if (okc) { st->status = ST_CONVERGED; st->ret_avg = 0; return; }
-    if (oka) { st->status = ST_CONVERGED; st->ret_avg = 1; return; }
+  if (threadIdx.x == 0) {
+    DevState *st = &S;
+    double q[16];
+    for (int k = 0; k < 16; ++k) q[k] = ((CK_MAXMASK >> k) & 1u) ? fmax(a[k], b[k]) : a[k] + b[k];
+    for (int k = 0; k < 16; ++k) st->chk[k] = q[k];
+    // The averages of this trial's acceptance were materialised by the check kernels.
+    st->acur ^= st->accepted;
+    st->accepted = 0;
+    st->restart_flag = 0;
+    const double dta = st->dta, dtr = st->dtr;
+    const double spc = fmax(1.0, q[1]), sdc = fmax(1.0, q[3]);
+    const double spa = fmax(1.0, q[9]), sda = fmax(1.0, q[11]);
+    const bool okc = q[0] <= dta + dtr * spc && q[2] <= dta + dtr * sdc;
+    const bool oka = q[8] <= dta + dtr * spa && q[10] <= dta + dtr * sda;
+    if (!st->ignore_conv && okc) {
+      st->status = ST_CONVERGED;
+      st->ret_avg = 0;
+    } else if (!st->ignore_conv && oka) {
+      st->status = ST_CONVERGED;
+      st->ret_avg = 1;
+    } else if (st->t_total == st->k_in) {
+      st->status = ST_ITER_LIMIT;
+    } else {
+      const double om = st->omega;
+      const double kc = sqrt(om * q[4] + q[5] / om);
+      const double ka = sqrt(om * q[12] + q[13] / om);
+      const bool use_avg = ka < kc;
+      const double kcand = use_avg ? ka : kc;
+      const bool restart = kcand <= st->beta_suff * st->k_restart ||
+                           (kcand <= st->beta_nec * st->k_restart && kcand > st->k_last) ||
+                           (double)st->t >= st->beta_art * (double)st->t_total;
+      st->k_last = kcand;
+      if (restart) {
+        const double dW = sqrt(use_avg ? q[14] : q[6]);
+        const double dY = sqrt(use_avg ? q[15] : q[7]);
+        if (dW > 0.0 && dY > 0.0) st->omega = exp(0.25 * log(dY / dW) + 0.75 * log(om));
+        st->kappa = 1.0;
+        st->t = 0;
+        st->k_restart = kcand;
+        st->k_last = INFINITY;
+        st->restarts += 1;
+        st->restart_flag = 1;
+        st->restart_use_avg = use_avg ? 1 : 0;
+      }
+      if (st->t_total == st->pause_at) st->status = ST_PAUSED;
+    }
+    if (hw) cudaGraphSetConditional(hw, (st->status == ST_RUNNING && st->slot_left > 0) ? 1u : 0u);
   }
-  if (st->t_total == st->k_in) { st->status = ST_ITER_LIMIT; return; }
-  const double om = st->omega;
-  const double kc = sqrt(om * q[4] + q[5] / om);
-  const double ka = sqrt(om * q[12] + q[13] / om);
-  const bool use_avg = ka < kc;
-  const double kcand = use_avg ? ka : kc;
-  const bool restart = kcand <= st->beta_suff * st->k_restart ||
-                       (kcand <= st->beta_nec * st->k_restart && kcand > st->k_last) ||
-                       (double)st->t >= st->beta_art * (double)st->t_total;
-  st->k_last = kcand;
-  if (restart) {
-    const double dW = sqrt(use_avg ? q[14] : q[6]);
-    const double dY = sqrt(use_avg ? q[15] : q[7]);
-    if (dW > 0.0 && dY > 0.0) st->omega = exp(0.25 * log(dY / dW) + 0.75 * log(om));
-    st->kappa = 1.0;
-    st->t = 0;
-    st->k_restart = kcand;
-    st->k_last = INFINITY;
-    st->restarts += 1;
-    st->restart_flag = 1;
-    st->restart_use_avg = use_avg ? 1 : 0;
-  }
-  if (st->t_total == st->pause_at) st->status = ST_PAUSED;
+  state_store(stg, S);
 }
 
 // Restart (Algorithm 4): optionally move the current point to the average

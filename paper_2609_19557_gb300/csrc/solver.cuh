@@ -48,7 +48,7 @@ struct Params {
   double kappa_shrink = 0.5;
   double delta_sigma = 2.0, sigma_max = 1e6, tol_floor = 0.1;
   double gamma_override = 0.0;
-  int chunk = 32;
+  int chunk = 128;
   long long iter_budget = 4000000000000000000LL;
   int g_rows = 0, g_cols = 0;  // lanes per CSR row (0 = from the mean row length)
 };
@@ -59,6 +59,7 @@ struct Result {
   long long outer = 0, inner = 0, trials = 0, restarts = 0, passes = 0;
   double seconds = 0, obj = 0;
   long long launches = 0;
+  double inner_seconds = 0, setup_seconds = 0;
 };
 
 class SolverBase {

@@ -19,22 +19,23 @@ namespace pdq {
     }                                                                             \
   } while (0)
 
+// K = entries per lane per CSR-stream chunk (chunk = 32 K nonzeros per warp).
+// Kernels are instantiated for K in {4, 8, 16}; GroupIter kernels read it as
+// lanes per row.
 template <typename F>
 static void with_G(int g, F f) {
   switch (g) {
-    case 1: f(std::integral_constant<int, 1>()); break;
-    case 2: f(std::integral_constant<int, 2>()); break;
     case 4: f(std::integral_constant<int, 4>()); break;
     case 8: f(std::integral_constant<int, 8>()); break;
-    case 16: f(std::integral_constant<int, 16>()); break;
-    default: f(std::integral_constant<int, 32>()); break;
+    default: f(std::integral_constant<int, 16>()); break;
   }
 }
 
+// K from the mean row length: the smallest power of two >= mean, in [4, 16].
 static int pick_g(long long nnz, long long rows) {
   const double mean = rows > 0 ? (double)nnz / (double)rows : 1.0;
-  int g = 2;
-  while (g < 32 && g < mean) g *= 2;
+  int g = 4;
+  while (g < 16 && g < mean) g *= 2;
   return g;
 }
 
@@ -454,16 +455,21 @@ class Solver : public SolverBase {
   void launch_cols() {
     with_G(gN_, [&](auto GG) { k_cols<T, decltype(GG)::value><<<nb_cols(), kBlock, 0, s_>>>(d_); });
   }
-  static constexpr int kSlotKernels = 9;
-  void launch_slot() {
+  static constexpr int kSlotKernels = 8;
+  void launch_trial(cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hc) {
     launch_primal();
     launch_rows();
     launch_cols();
-    k_decide<<<1, kRedThreads, 0, s_>>>(st_, part_, nb_rows(), nb_cols());
-    k_average<T><<<grid_nm(), kBlock, 0, s_>>>(d_);
+    k_decide<<<1, kRedThreads, 0, s_>>>(st_, part_, nb_rows(), nb_cols(), hw, hc);
+  }
+  void launch_check_group(cudaGraphConditionalHandle hw) {
     launch_check(0);
-    k_check_final<<<1, kRedThreads, 0, s_>>>(st_, part_, nb_rows(), nb_cols());
+    k_check_final<<<1, kRedThreads, 0, s_>>>(st_, part_, nb_rows(), nb_cols(), hw);
     k_check_apply<T><<<grid_nm(), kBlock, 0, s_>>>(d_);
+  }
+  void launch_slot() {
+    launch_trial(0, 0);
+    launch_check_group(0);
   }
   void launch_check(int mode) {
     with_G(gA_, [&](auto GG) { k_check_rows<T, decltype(GG)::value><<<nb_rows(), kBlock, 0, s_>>>(d_, mode); });
@@ -484,6 +490,10 @@ class Solver : public SolverBase {
       cudaGraphExecDestroy(gexec_);
       gexec_ = nullptr;
     }
+    graph_chunk_ = chunk;
+    if (use_cond_ && build_graph_cond(chunk) == 0) return 0;
+    use_cond_ = false;  // conditional nodes unavailable: unrolled slots
+    cudaGetLastError();
     cudaGraph_t g;
     PDNQP_CK(cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < chunk; ++k) launch_slot();
@@ -494,7 +504,72 @@ class Solver : public SolverBase {
       last_err_ = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
       return PDNQP_ERR_CUDA;
     }
-    graph_chunk_ = chunk;
+    return 0;
+  }
+
+  // Device-driven loop: [begin] -> WHILE(hw) { primal, rows, cols, decide,
+  // IF(hc) { check-rows, check-cols, check-final, check-apply } }.  decide
+  // sets hw (continue while running and fewer than `chunk` trials ran in this
+  // launch) and hc (a check is due); check-final updates hw.  Every launch
+  // therefore ends after at most `chunk` trials.
+  int build_graph_cond(int chunk) {
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return -1;
+    auto fail = [&]() {
+      cudaStreamCaptureStatus cs;
+      if (cudaStreamIsCapturing(s_, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+        cudaGraph_t junk;
+        cudaStreamEndCapture(s_, &junk);
+        if (junk) cudaGraphDestroy(junk);
+      }
+      cudaGraphDestroy(g);
+      cudaGetLastError();
+      return -1;
+    };
+    cudaGraphConditionalHandle hw, hc;
+    if (cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) return fail();
+    if (cudaGraphConditionalHandleCreate(&hc, g, 0, cudaGraphCondAssignDefault) != cudaSuccess) return fail();
+    if (cudaStreamBeginCaptureToGraph(s_, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return fail();
+    k_loop_begin<<<1, 1, 0, s_>>>(st_, (long long)chunk);
+    if (cudaStreamEndCapture(s_, &g) != cudaSuccess) return fail();
+    cudaGraphNode_t begin;
+    size_t nn = 1;
+    if (cudaGraphGetNodes(g, &begin, &nn) != cudaSuccess || nn != 1) return fail();
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hw;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    if (cudaGraphAddNode(&wnode, g, &begin, nullptr, 1, &wp) != cudaSuccess) return fail();
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(s_, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return fail();
+    launch_trial(hw, hc);
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    if (cudaStreamGetCaptureInfo(s_, &cst, nullptr, nullptr, &deps, nullptr, &ndeps) != cudaSuccess) return fail();
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hc;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t inode;
+    if (cudaGraphAddNode(&inode, body, deps, nullptr, ndeps, &ip) != cudaSuccess) return fail();
+    if (cudaStreamUpdateCaptureDependencies(s_, &inode, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+      return fail();
+    cudaGraph_t body_out = nullptr;
+    if (cudaStreamEndCapture(s_, &body_out) != cudaSuccess) return fail();
+    cudaGraph_t cbody = ip.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(s_, cbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return fail();
+    launch_check_group(hw);
+    cudaGraph_t cbody_out = nullptr;
+    if (cudaStreamEndCapture(s_, &cbody_out) != cudaSuccess) return fail();
+    if (cudaGraphInstantiate(&gexec_, g, 0) != cudaSuccess) return fail();
+    cudaGraphDestroy(g);
     return 0;
   }
 
@@ -563,10 +638,11 @@ class Solver : public SolverBase {
     if (m_) with_G(gA_, [&](auto GG) { k_my_rows<T, decltype(GG)::value><<<nb_rows(), kBlock, 0, s_>>>(d_, scn_[0]); });
     with_G(gN_, [&](auto GG) { k_cache_cols<T, decltype(GG)::value><<<nb_cols(), kBlock, 0, s_>>>(d_); });
     k_inner_init<T><<<grid_nm(), kBlock, 0, s_>>>(d_);
-    // Device state of this solve.
-    DevState S;
-    PDNQP_CK(cudaMemcpyAsync(&S, st_, sizeof(S), cudaMemcpyDeviceToHost, s_));
-    PDNQP_CK(cudaStreamSynchronize(s_));
+    // Device state of this solve (the host holds every field it needs; the
+    // iterates sit in buffer 0 between inner solves).
+    DevState &S = *hst_;
+    memset(&S, 0, sizeof(S));
+    S.cur = 0;
     S.status = ST_IDLE;
     S.accepted = 0;
     S.acur = 0;
@@ -611,10 +687,21 @@ class Solver : public SolverBase {
   // Runs graph chunks until the device status leaves RUNNING.
   int run_until_stop(const Params &prm, DevState *S, double t0) {
     PDNQP_TRY(build_graph(prm.chunk));
+    long long tr0 = -1, ac0 = 0;
     for (;;) {
       PDNQP_CK(cudaGraphLaunch(gexec_, s_));
-      launches_ += (long long)prm.chunk * kSlotKernels;
       PDNQP_TRY(read_state(S));
+      if (use_cond_) {
+        // 4 kernels per trial, 4 more per check, 1 loop-begin kernel per launch.
+        if (tr0 < 0) tr0 = trials_, ac0 = accepted_;
+        launches_ += 1;
+        launches_ += 4 * (S->trials - tr0) + 4 * ((S->accepted_all / std::max<long long>(1, prm.k_chk)) -
+                                                  (ac0 / std::max<long long>(1, prm.k_chk)));
+        tr0 = S->trials;
+        ac0 = S->accepted_all;
+      } else {
+        launches_ += (long long)prm.chunk * kSlotKernels;
+      }
       if (S->status != ST_RUNNING) return 0;
       if (seconds_since(t0) > prm.time_limit) return 1;
     }
@@ -653,23 +740,26 @@ class Solver : public SolverBase {
     const double ginv = 1.0 / gamma_;
     launches_ += 4;
     double a[12] = {0}, b[12] = {0};
+    const int nbr = nb_rows(), nbc = nb_cols();
     if (m_) {
-      const int nb = nb_rows();
       with_G(gA_, [&](auto GG) {
-        k_outer_rows<T, decltype(GG)::value><<<nb, kBlock, 0, s_>>>(d_, Ad_, lcd_, ucd_, Dc_, lam_, sig_, rcur_,
-                                                                     update);
+        k_outer_rows<T, decltype(GG)::value><<<nbr, kBlock, 0, s_>>>(d_, Ad_, lcd_, ucd_, Dc_, lam_, sig_, rcur_,
+                                                                      update);
       });
-      PDNQP_TRY(reduce_to_host(12, nb, OUT_MAXMASK, a));
+      k_reduce_rows<<<1, kRedThreads, 0, s_>>>(part_, 12, nbr, OUT_MAXMASK, dred_);
     }
-    const int nb = nb_cols();
+    // A' lambda uses the updated multipliers: launched after the row kernel.
     with_G(gN_, [&](auto GG) {
-      k_outer_cols<T, decltype(GG)::value><<<nb, kBlock, 0, s_>>>(d_, Hd_, Atd_, c_, lxd_, uxd_, Dx_, lam_, z_,
-                                                                   ginv, cs_);
+      k_outer_cols<T, decltype(GG)::value><<<nbc, kBlock, 0, s_>>>(d_, Hd_, Atd_, c_, lxd_, uxd_, Dx_, lam_, z_,
+                                                                    ginv, cs_);
     });
-    k_reduce_rows<<<1, kRedThreads, 0, s_>>>(part_ + 12 * kMaxBlocks, 12, nb, OUT_MAXMASK, dred_);
-    PDNQP_CK(cudaMemcpyAsync(hred_.data(), dred_, sizeof(double) * 12, cudaMemcpyDeviceToHost, s_));
+    k_reduce_rows<<<1, kRedThreads, 0, s_>>>(part_ + 12 * kMaxBlocks, 12, nbc, OUT_MAXMASK, dred_ + 12);
+    PDNQP_CK(cudaGetLastError());
+    PDNQP_CK(cudaMemcpyAsync(hred_.data(), dred_, sizeof(double) * 24, cudaMemcpyDeviceToHost, s_));
     PDNQP_CK(cudaStreamSynchronize(s_));
-    for (int k = 0; k < 12; ++k) b[k] = hred_[k];
+    if (m_)
+      for (int k = 0; k < 12; ++k) a[k] = hred_[k];
+    for (int k = 0; k < 12; ++k) b[k] = hred_[12 + k];
     for (int k = 0; k < 12; ++k) q[k] = ((OUT_MAXMASK >> k) & 1u) ? std::max(a[k], b[k]) : a[k] + b[k];
     return 0;
   }
@@ -682,6 +772,7 @@ class Solver : public SolverBase {
       gamma_pending_ = 0;
     }
     launches_ = 0;
+    double t_setup = 0.0, t_inner = 0.0;
     apply_g(prm);
     PDNQP_TRY(start_point(prm));
     double dta = 1.0, dtr = 1.0, eak = 1.0, erk = 1.0;
@@ -698,10 +789,15 @@ class Solver : public SolverBase {
         status = PDNQP_ITER_LIMIT;
         break;
       }
+      const double ts0 = now();
       PDNQP_TRY(inner_setup(prm, dta, dtr, std::min(prm.k_in, left), -1, 0));
+      PDNQP_CK(cudaStreamSynchronize(s_));
+      const double ts1 = now();
+      t_setup += ts1 - ts0;
       DevState S;
       int tl = 0;
       PDNQP_TRY(tl = run_until_stop(prm, &S, t0));
+      t_inner += now() - ts1;
       if (tl == 1) {
         // time limit inside the inner solve: stop the device loop
         PDNQP_TRY(read_state(&S));
@@ -764,6 +860,8 @@ class Solver : public SolverBase {
     res_.passes = 3 * trials_ + 2 * (accepted_ / std::max(1, prm.k_chk));
     res_.seconds = seconds_since(t0);
     res_.launches = launches_;
+    res_.inner_seconds = t_inner;
+    res_.setup_seconds = t_setup;
     solved_once_ = true;
     return status;
   }
@@ -827,6 +925,10 @@ class Solver : public SolverBase {
       int tl = 0;
       PDNQP_TRY(tl = run_until_stop(prm, &S, t0));
       if (tl == 1 || S.status != ST_PAUSED) break;
+      if (S.accepted) {  // materialise the pending running averages before reading them
+        k_average<T><<<grid_nm(), kBlock, 0, s_>>>(d_);
+        PDNQP_CK(cudaGetLastError());
+      }
       PDNQP_TRY(snapshot(S, snap + (long long)got * len));
       ++got;
       S.status = ST_RUNNING;
@@ -861,6 +963,7 @@ class Solver : public SolverBase {
   Dev<T> d_{};
   cudaGraphExec_t gexec_ = nullptr;
   int graph_chunk_ = 0;
+  bool use_cond_ = true;  // device-driven WHILE/IF graph (else unrolled slots)
   double cs_ = 1.0, qnorm_ = 0.0, gamma_ = 1.0, lam_min_ = 0.0, sigma0_ = 1.0, omega_ = 1.0;
   double gamma_pending_ = 0.0;
   long long trials_ = 0, accepted_ = 0, restarts_ = 0, launches_ = 0;

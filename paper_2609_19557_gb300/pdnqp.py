@@ -37,7 +37,8 @@ class pdnqp_residuals(C.Structure):
                 ("rel_kkt", C.c_double), ("outer_iters", C.c_int64), ("inner_iters", C.c_int64),
                 ("trials", C.c_int64), ("restarts", C.c_int64), ("kkt_passes", C.c_int64),
                 ("solve_seconds", C.c_double), ("gamma", C.c_double), ("lambda_min", C.c_double),
-                ("obj", C.c_double), ("kernel_launches", C.c_int64)]
+                ("obj", C.c_double), ("kernel_launches", C.c_int64),
+                ("inner_seconds", C.c_double), ("setup_seconds", C.c_double)]
 
 
 class pdnqp_options(C.Structure):
