@@ -185,6 +185,45 @@ PDNQP_API int pdnqp_replay_kernel(pdnqp_t *h, int which, int reps);
  * (which = -1), for the roofline. */
 PDNQP_API int pdnqp_kernel_bytes(const pdnqp_t *h, int which, double *bytes);
 
+/* ------------------------------------------------------------------------ */
+/* External KKT test on device data.                                        */
+/* ------------------------------------------------------------------------ */
+/* CSR matrix whose three arrays live in DEVICE memory (same layout rules as
+ * pdnqp_csr). */
+typedef struct {
+  int32_t n_rows;
+  int32_t n_cols;
+  int64_t nnz;
+  const int32_t *row_ptr;
+  const int32_t *col_idx;
+  const double *val;
+} pdnqp_device_csr;
+
+/* Eq. qp with every array in DEVICE memory: Q (n x n, symmetric, both
+ * triangles), A (m x n) and its transpose At (n x m) -- A^T y is computed
+ * row-wise from At, without atomics -- and the vectors c, l_x, u_x (n) and
+ * l_c, u_c (m).  m may be 0 (A, At, l_c, u_c unused).  The caller owns all
+ * arrays. */
+typedef struct {
+  pdnqp_device_csr Q, A, At;
+  const double *c, *l_c, *u_c, *l_x, *u_x;
+} pdnqp_device_problem;
+
+/* External KKT test of Sec. 4.1 for the point (x, y) (device arrays, n and m
+ * doubles, y in the sign convention of pdnqp_get): writes out[0..3] = r_p,
+ * r_d, s_p, s_d of Eqs. outer-residuals / outer-scales on the given (original)
+ * data, with variable-bound violations counted in r_p; out is a DEVICE
+ * pointer to 4 doubles.  A point passes at tolerances (eps_a, eps_r) when
+ * r_p <= eps_a + eps_r s_p and r_d <= eps_a + eps_r s_d (Eq. outer-termination).  The work is issued on `stream` (cudaStream_t,
+ * NULL = legacy default stream) and the call returns after the stream has
+ * finished it.  Scratch for the block partial sums (5 x 1216 doubles) is
+ * allocated with cudaMalloc and freed inside the call.  Returns 0 or a
+ * negative error code; the message is available from pdnqp_kkt_last_error
+ * (thread-local). */
+PDNQP_API int pdnqp_kkt_residuals(const pdnqp_device_problem *P, const double *x, const double *y, double *out,
+                                  void *stream);
+PDNQP_API const char *pdnqp_kkt_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

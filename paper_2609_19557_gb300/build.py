@@ -1,6 +1,6 @@
 """Builds the CUDA library libpdnqp.so in-tree (paper_2609_19557_gb300/_build/).
 
-Three translation units (C ABI, FP64 solver, FP32-bulk solver) are compiled
+Four translation units (C ABI, FP64 solver, FP32-bulk solver, KKT test) are compiled
 in parallel with nvcc for sm_103a only, then linked into one shared library
 with the CUDA runtime linked statically.
 """
@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpdnqp.so")
-SOURCES = ["api.cu", "solver_f64.cu", "solver_f32.cu"]
+SOURCES = ["api.cu", "solver_f64.cu", "solver_f32.cu", "kkt_check.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-O2",
          "-Xcompiler", "-fvisibility=hidden"]

@@ -24,7 +24,7 @@ SNAP_SCALARS = 8
 # Every function declared in include/pdnqp.h.
 EXPORTED = ["pdnqp_create", "pdnqp_create_ex", "pdnqp_destroy", "pdnqp_solve", "pdnqp_get", "pdnqp_set_start",
             "pdnqp_set_param", "pdnqp_get_param", "pdnqp_dims", "pdnqp_last_error", "pdnqp_debug_inner",
-            "pdnqp_replay_kernel", "pdnqp_kernel_bytes"]
+            "pdnqp_replay_kernel", "pdnqp_kernel_bytes", "pdnqp_kkt_residuals", "pdnqp_kkt_last_error"]
 
 
 class pdnqp_csr(C.Structure):
@@ -39,6 +39,17 @@ class pdnqp_residuals(C.Structure):
                 ("solve_seconds", C.c_double), ("gamma", C.c_double), ("lambda_min", C.c_double),
                 ("obj", C.c_double), ("kernel_launches", C.c_int64),
                 ("inner_seconds", C.c_double), ("setup_seconds", C.c_double)]
+
+
+class pdnqp_device_csr(C.Structure):
+    _fields_ = [("n_rows", C.c_int32), ("n_cols", C.c_int32), ("nnz", C.c_int64),
+                ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("val", C.c_void_p)]
+
+
+class pdnqp_device_problem(C.Structure):
+    _fields_ = [("Q", pdnqp_device_csr), ("A", pdnqp_device_csr), ("At", pdnqp_device_csr),
+                ("c", C.c_void_p), ("l_c", C.c_void_p), ("u_c", C.c_void_p), ("l_x", C.c_void_p),
+                ("u_x", C.c_void_p)]
 
 
 class pdnqp_options(C.Structure):
@@ -77,6 +88,9 @@ def load(path: str | None = None):
     L.pdnqp_debug_inner.argtypes = [vp, ip, vp, vp]
     L.pdnqp_replay_kernel.argtypes = [vp, ip, ip]
     L.pdnqp_kernel_bytes.argtypes = [vp, ip, C.POINTER(C.c_double)]
+    L.pdnqp_kkt_residuals.argtypes = [C.POINTER(pdnqp_device_problem), vp, vp, vp, vp]
+    L.pdnqp_kkt_last_error.argtypes = []
+    L.pdnqp_kkt_last_error.restype = C.c_char_p
     for name in EXPORTED:
         if not hasattr(L, name):
             raise PdnqpError(f"{p} does not export {name}")
@@ -216,3 +230,37 @@ def create_from_instance(inst: dict, precision: int = PDNQP_FP64, stream=None) -
     """Convenience: handle for an instance dict as produced by instances.py."""
     return pdnqp_create(inst["Q"], inst["c"], inst["A"], inst["l_c"], inst["u_c"], inst["l_x"], inst["u_x"],
                         precision=precision, stream=stream)
+
+
+class DeviceProblem:
+    """Eq. qp copied to the current CUDA device with torch (device memory only);
+    keeps the tensors alive while the C struct points at them."""
+
+    def __init__(self, inst: dict):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        Q, A = inst["Q"].tocsr(), inst["A"].tocsr()
+        At = A.T.tocsr()
+        i32 = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.int32), device=dev)
+        f64 = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+        self.t = {}
+
+        def csr(M, name):
+            rp, ci, v = i32(M.indptr), i32(M.indices), f64(M.data)
+            self.t[name] = (rp, ci, v)
+            return pdnqp_device_csr(M.shape[0], M.shape[1], int(M.nnz), rp.data_ptr(), ci.data_ptr(), v.data_ptr())
+
+        vec = {k: f64(inst[k]) for k in ("c", "l_c", "u_c", "l_x", "u_x")}
+        self.t.update(vec)
+        self.s = pdnqp_device_problem(csr(Q, "Q"), csr(A, "A"), csr(At, "At"), vec["c"].data_ptr(),
+                                      vec["l_c"].data_ptr(), vec["u_c"].data_ptr(), vec["l_x"].data_ptr(),
+                                      vec["u_x"].data_ptr())
+        self.n, self.m = Q.shape[0], A.shape[0]
+
+
+def pdnqp_kkt_residuals(prob: DeviceProblem, x, y, out, stream=None):
+    """x, y, out: torch float64 CUDA tensors (out has 4 entries)."""
+    rc = load().pdnqp_kkt_residuals(C.byref(prob.s), x.data_ptr(), y.data_ptr() if prob.m else None, out.data_ptr(),
+                                    C.c_void_p(int(stream)) if stream else None)
+    if rc < 0:
+        raise PdnqpError(f"pdnqp_kkt_residuals error {rc}: {load().pdnqp_kkt_last_error().decode()}")
