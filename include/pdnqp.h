@@ -224,6 +224,31 @@ PDNQP_API int pdnqp_kkt_residuals(const pdnqp_device_problem *P, const double *x
                                   void *stream);
 PDNQP_API const char *pdnqp_kkt_last_error(void);
 
+/* The same external KKT test without any device allocation, for callers that
+ * cannot call cudaMalloc / cudaFree: for example code running inside a
+ * runtime whose memory manager owns all device memory, or latency-critical
+ * loops that cannot take the device-wide synchronisation of cudaFree.  The
+ * paper has no counterpart; it is a variant of pdnqp_kkt_residuals.
+ * Differences from pdnqp_kkt_residuals:
+ *   - Scratch: a file-scope __device__ array of 5 x 1216 doubles (48,640
+ *     bytes) that every GPU loading the library holds until the process
+ *     exits.  Every problem that fits the int32 CSR layout is accepted (the
+ *     kernels stride over rows with at most 1216 blocks); larger ones are
+ *     rejected with PDNQP_ERR_ARG and a message.
+ *   - Set-up: the first call on each device looks up the device address of
+ *     that array (cudaGetSymbolAddress) with the device current; make that
+ *     first call before any stream capture.
+ *   - All calls on a device share the array and it keeps the last call's
+ *     contents (no clearing is needed: each call writes every entry it
+ *     reads).  Calls that overlap on the GPU (other streams, other host
+ *     threads) race on it and must be serialised by the caller.
+ *   - Asynchronous: the work is enqueued on `stream` and the call returns
+ *     without waiting; out holds the residuals once the stream has reached
+ *     this work, and execution errors surface at the next synchronisation.
+ * Arguments, layout and return codes are those of pdnqp_kkt_residuals. */
+PDNQP_API int pdnqp_kkt_residuals_noalloc(const pdnqp_device_problem *P, const double *x, const double *y,
+                                          double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

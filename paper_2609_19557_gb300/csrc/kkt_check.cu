@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
 #include <string>
 
 #include "../../include/pdnqp.h"
@@ -60,10 +61,69 @@ int launch_kkt(const pdnqp_device_problem *P, const double *x, const double *y, 
   return 0;
 }
 
+// Scratch of pdnqp_kkt_residuals_noalloc: the block partial sums of one call,
+// kKktQ quantities x kMaxBlocks blocks = 5 x 1216 doubles (48,640 bytes).
+// Every device that loads the library holds this array until the process
+// exits; all calls on a device share it.
+static __device__ __align__(256) double g_kkt_noalloc_scratch[kKktQ * kMaxBlocks];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the static scratch on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+int noalloc_scratch(double **out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    g_kkt_err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    return PDNQP_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    g_kkt_err = "device ordinal out of range for the static scratch table";
+    return PDNQP_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_kkt_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      g_kkt_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+      return PDNQP_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = (double *)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return 0;
+}
+
 }  // namespace
 }  // namespace pdq
 
 extern "C" {
+
+int pdnqp_kkt_residuals_noalloc(const pdnqp_device_problem *P, const double *x, const double *y, double *out,
+                                void *stream) {
+  using namespace pdq;
+  int rc = check_problem(P, x, y, out);
+  if (rc) return rc;
+  // Each pass launches at most kMaxBlocks blocks (grid-stride over rows), so
+  // the partial sums of any problem that fits the int32 CSR layout fit the
+  // static array; a grid that would not fit is rejected.
+  const int nb_r = grid_for(P->A.n_rows > 0 ? P->A.n_rows : 1, kBlock), nb_c = grid_for(P->Q.n_rows, kBlock);
+  if (nb_r > kMaxBlocks || nb_c > kMaxBlocks) {
+    g_kkt_err = "problem needs more partial sums than the static scratch holds (5 x 1216)";
+    return PDNQP_ERR_ARG;
+  }
+  double *scratch = nullptr;
+  rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  // Every block writes its partial sums before the final kernel reads exactly
+  // those entries, so nothing left by a previous call needs clearing.
+  return launch_kkt(P, x, y, out, scratch, (cudaStream_t)stream);
+}
 
 int pdnqp_kkt_residuals(const pdnqp_device_problem *P, const double *x, const double *y, double *out,
                         void *stream) {

@@ -24,7 +24,8 @@ SNAP_SCALARS = 8
 # Every function declared in include/pdnqp.h.
 EXPORTED = ["pdnqp_create", "pdnqp_create_ex", "pdnqp_destroy", "pdnqp_solve", "pdnqp_get", "pdnqp_set_start",
             "pdnqp_set_param", "pdnqp_get_param", "pdnqp_dims", "pdnqp_last_error", "pdnqp_debug_inner",
-            "pdnqp_replay_kernel", "pdnqp_kernel_bytes", "pdnqp_kkt_residuals", "pdnqp_kkt_last_error"]
+            "pdnqp_replay_kernel", "pdnqp_kernel_bytes", "pdnqp_kkt_residuals", "pdnqp_kkt_last_error",
+            "pdnqp_kkt_residuals_noalloc"]
 
 
 class pdnqp_csr(C.Structure):
@@ -89,6 +90,7 @@ def load(path: str | None = None):
     L.pdnqp_replay_kernel.argtypes = [vp, ip, ip]
     L.pdnqp_kernel_bytes.argtypes = [vp, ip, C.POINTER(C.c_double)]
     L.pdnqp_kkt_residuals.argtypes = [C.POINTER(pdnqp_device_problem), vp, vp, vp, vp]
+    L.pdnqp_kkt_residuals_noalloc.argtypes = [C.POINTER(pdnqp_device_problem), vp, vp, vp, vp]
     L.pdnqp_kkt_last_error.argtypes = []
     L.pdnqp_kkt_last_error.restype = C.c_char_p
     for name in EXPORTED:
@@ -264,3 +266,11 @@ def pdnqp_kkt_residuals(prob: DeviceProblem, x, y, out, stream=None):
                                     C.c_void_p(int(stream)) if stream else None)
     if rc < 0:
         raise PdnqpError(f"pdnqp_kkt_residuals error {rc}: {load().pdnqp_kkt_last_error().decode()}")
+
+
+def pdnqp_kkt_residuals_noalloc(prob: DeviceProblem, x, y, out, stream=None):
+    """Allocation-free variant (static device scratch); asynchronous on `stream`."""
+    rc = load().pdnqp_kkt_residuals_noalloc(C.byref(prob.s), x.data_ptr(), y.data_ptr() if prob.m else None,
+                                            out.data_ptr(), C.c_void_p(int(stream)) if stream else None)
+    if rc < 0:
+        raise PdnqpError(f"pdnqp_kkt_residuals_noalloc error {rc}: {load().pdnqp_kkt_last_error().decode()}")
