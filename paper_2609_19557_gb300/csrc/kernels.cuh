@@ -3,7 +3,13 @@
 // iterates and matrix values (double: plain FP64 form; float: FP32-bulk form).
 //
 // Coordinates.  The inner iterates live in the outer-scaled, inner-UNSCALED
-// coordinates of Eq. inner-qp: w = (x, s_I, r_E, r_I), y.  The penalty scaling
+// coordinates of Eq. inner-qp: w = (x, s_I, r_E, r_I), y, stored as
+// corrections from the FP64 base point of the solve (the warm start w_b, y_b):
+// w = w_b + dw, y = y_b + dy.  The base enters only through the gradient of
+// the inner objective at the base (q' = q + H w_b - B'y_b), the residual
+// h' = h - B w_b and the shifted bounds, so the iteration is exactly PDHG on
+// (dw, dy) and the FP32-bulk form keeps full relative precision in the
+// corrections.  The penalty scaling
 // (Eq. inner-penalty-scaling) and the inner Ruiz scaling (Sec. 3.3.2) are the
 // diagonal change of variables w = E w~, y = D y~; PDHG in the scaled space is
 // exactly PDHG in these coordinates with the effective diagonal steps
@@ -44,14 +50,24 @@ template <typename T>
 struct Dev {
   int n, m, mE;
   Mat<T> H, A, At;  // H = Qbar + gamma^-1 I (x block of H_k), A (rows E then I), A^T
-  // n-vectors
+  // n-vectors: corrections dx and their cached products H dx, A' dy, averages
   T *x[2], *Hx[2], *Aty[2], *xbar[2], *Hxbar[2];
-  T *qx, *lx, *ux, *taux, *itaux, *ex, *xst, *Atybar;
+  T *qx;          // q'_x = c - z / gamma + H x_b - A' y_b
+  T *qx0;         // q_x = c - z / gamma (scale s_d)
+  T *Hxb, *Atyb;  // H x_b, A' y_b (scales)
+  T *lx, *ux;     // shifted bounds l - x_b, u - x_b
+  T *taux, *itaux, *ex, *xst, *Atybar;
   // m-vectors (s is indexed by row; entries of equality rows are unused)
   T *y[2], *s[2], *r[2], *Bw[2], *ybar[2], *sbar[2], *rbar[2];
-  T *eta, *taus, *taur, *ieta, *itaus, *itaur, *es, *er, *dy, *h, *ls, *us, *yst, *sst, *rst, *Bwbar;
-  // FP64 outer data: multipliers lambda and row penalties sigma
-  const double *lam, *sig;
+  T *qs;          // y_b: gradient of the s block at the base (I rows)
+  T *qr;          // lambda + sigma r_b + y_b: gradient of the r block at the base
+  T *hp;          // h - B w_b
+  T *h, *Bwb;     // h and B w_b (scale s_p)
+  T *ls, *us;     // shifted slack bounds l_c - s_b, u_c - s_b (I rows)
+  T *eta, *taus, *taur, *ieta, *itaus, *itaur, *es, *er, *dy, *yst, *sst, *rst, *Bwbar;
+  // FP64 base point and outer data
+  const double *xb, *yb, *sb, *rb;  // base: outer x, inner y, warm-start s and r
+  const double *lam, *sig;          // multipliers and row penalties
   double *part;
   DevState *st;
 };
@@ -146,19 +162,19 @@ __global__ void __launch_bounds__(kBlock) k_rows(Dev<T> d) {
       } else {
         rb = d.rbar[a0][j];
       }
-      const T lam = T(d.lam[j]), sig = T(d.sig[j]);
-      const T rt = r - (sct * d.taur[j]) * (lam + sig * (oma * rb + alpha * r) + y);
+      const T sig = T(d.sig[j]);
+      const T rt = r - (sct * d.taur[j]) * (d.qr[j] + sig * (oma * rb + alpha * r) + y);
       T bwt = ax - rt, ds = T(0);
       if (j >= d.mE) {
         const T s = d.s[cur][j];
-        const T stv = clampv<T>(s - (sct * d.taus[j]) * y, d.ls[j], d.us[j]);
+        const T stv = clampv<T>(s - (sct * d.taus[j]) * (d.qs[j] + y), d.ls[j], d.us[j]);
         d.s[nx][j] = stv;
         bwt -= stv;
         ds = stv - s;
         Lt += ds * ds * d.itaus[j];
       }
       const T bw = d.Bw[cur][j];
-      const T yt = y + (sce * d.eta[j]) * (d.h[j] - bwt - beta * (bwt - bw));
+      const T yt = y + (sce * d.eta[j]) * (d.hp[j] - bwt - beta * (bwt - bw));
       d.r[nx][j] = rt;
       d.Bw[nx][j] = bwt;
       d.y[nx][j] = yt;
@@ -308,42 +324,48 @@ __global__ void __launch_bounds__(kBlock) k_average(Dev<T> d) {
 // stored as [c0..c7, a0..a7].  mode 1 = only the current point's 4 and 5
 // (restart metric of the inner start).
 // ===========================================================================
-template <typename T>
-struct RowCand {
-  // s/r/y contributions of one row to the 8 quantities of one candidate.
-  __device__ static void add(double *q, bool is_ineq, T bw, T h, T s, T r, T y, T lam, T sig, T ls, T us, T es,
-                             T er, T dyv, T sst, T rst, T yst) {
-    const double e_bh = double(bw) - double(h);
-    q[0] = fmax(q[0], fabs(e_bh));
-    q[1] = fmax(q[1], fmax(fabs(double(bw)), fabs(double(h))));
-    const double gr = double(sig) * double(r) + double(lam) + double(y);
-    q[2] = fmax(q[2], fabs(gr));
-    q[3] = fmax(q[3], fmax(fabs(double(sig) * double(r)), fmax(fabs(double(lam)), fabs(double(y)))));
-    q[4] += (double(dyv) * e_bh) * (double(dyv) * e_bh);
-    q[5] += (double(er) * gr) * (double(er) * gr);
-    const double wr = (double(r) - double(rst)) / double(er);
-    q[6] += wr * wr;
-    const double wy = (double(y) - double(yst)) / double(dyv);
-    q[7] += wy * wy;
-    if (is_ineq) {
-      const double gs = double(y);
-      const double sv = double(s);
-      const double lo = double(ls), hi = double(us);
-      double p = sv - gs;
-      p = p < lo ? lo : p;
-      p = p > hi ? hi : p;
-      q[2] = fmax(q[2], fabs(sv - p));
-      const double e2 = double(es) * double(es);
-      double p2 = sv - e2 * gs;
-      p2 = p2 < lo ? lo : p2;
-      p2 = p2 > hi ? hi : p2;
-      const double ks = (sv - p2) / double(es);
-      q[5] += ks * ks;
-      const double ws = (sv - double(sst)) / double(es);
-      q[6] += ws * ws;
-    }
-  }
+// Contributions of one row (its s and r components and its dual) to the 8
+// quantities of one candidate, in FP64.  Inputs are corrections (bwd = B dw,
+// ds, dr, dy, epoch-start corrections) plus the base data of the row.
+struct RowIn {
+  bool ineq;
+  double bwd, hp, bwb, h;        // B dw, h - B w_b, B w_b, h
+  double ds, dr, dyv;            // corrections
+  double qs, qr, sig, lam;       // base gradients (s, r blocks), penalty, multiplier
+  double rb, yb;                 // base r and y
+  double ls, us;                 // shifted slack bounds
+  double es, er, dsc;            // column scales of s, r and the row scale
+  double sst, rst, yst;          // epoch-start corrections
 };
+
+__device__ __forceinline__ void row_cand(double *q, const RowIn &a) {
+  const double e_bh = a.bwd - a.hp;  // (B w - h)_j
+  q[0] = fmax(q[0], fabs(e_bh));
+  q[1] = fmax(q[1], fmax(fabs(a.bwb + a.bwd), fabs(a.h)));
+  const double gr = a.qr + a.sig * a.dr + a.dyv;  // sigma r + lambda + y at the point
+  q[2] = fmax(q[2], fabs(gr));
+  q[3] = fmax(q[3], fmax(fabs(a.sig * (a.rb + a.dr)), fmax(fabs(a.lam), fabs(a.yb + a.dyv))));
+  q[4] += (a.dsc * e_bh) * (a.dsc * e_bh);
+  q[5] += (a.er * gr) * (a.er * gr);
+  const double wr = (a.dr - a.rst) / a.er;
+  q[6] += wr * wr;
+  const double wy = (a.dyv - a.yst) / a.dsc;
+  q[7] += wy * wy;
+  if (a.ineq) {
+    const double gs = a.qs + a.dyv;  // y at the point
+    double p = a.ds - gs;
+    p = p < a.ls ? a.ls : p;
+    p = p > a.us ? a.us : p;
+    q[2] = fmax(q[2], fabs(a.ds - p));
+    double p2 = a.ds - a.es * a.es * gs;
+    p2 = p2 < a.ls ? a.ls : p2;
+    p2 = p2 > a.us ? a.us : p2;
+    const double ks = (a.ds - p2) / a.es;
+    q[5] += ks * ks;
+    const double ws = (a.ds - a.sst) / a.es;
+    q[6] += ws * ws;
+  }
+}
 
 template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_check_rows(Dev<T> d, int mode) {
@@ -368,13 +390,30 @@ __global__ void __launch_bounds__(kBlock) k_check_rows(Dev<T> d, int mode) {
     const long long j = tile + ti.lane;
     if (j < d.m) {
       const bool ineq = j >= d.mE;
-      const T h = d.h[j], lam = T(d.lam[j]), sig = T(d.sig[j]);
-      const T ls = ineq ? d.ls[j] : T(0), us = ineq ? d.us[j] : T(0), es = ineq ? d.es[j] : T(1);
-      const T er = d.er[j], dyv = d.dy[j];
-      const T sst = ineq ? d.sst[j] : T(0), rst = d.rst[j], yst = d.yst[j];
-      const T sc = ineq ? d.s[cur][j] : T(0);
-      RowCand<T>::add(q, ineq, d.Bw[cur][j], h, sc, d.r[cur][j], d.y[cur][j], lam, sig, ls, us, es, er, dyv, sst,
-                      rst, yst);
+      RowIn a;
+      a.ineq = ineq;
+      a.hp = double(d.hp[j]);
+      a.bwb = double(d.Bwb[j]);
+      a.h = double(d.h[j]);
+      a.qs = ineq ? double(d.qs[j]) : 0.0;
+      a.qr = double(d.qr[j]);
+      a.sig = d.sig[j];
+      a.lam = d.lam[j];
+      a.rb = d.rb[j];
+      a.yb = d.yb[j];
+      a.ls = ineq ? double(d.ls[j]) : 0.0;
+      a.us = ineq ? double(d.us[j]) : 0.0;
+      a.es = ineq ? double(d.es[j]) : 1.0;
+      a.er = double(d.er[j]);
+      a.dsc = double(d.dy[j]);
+      a.sst = ineq ? double(d.sst[j]) : 0.0;
+      a.rst = double(d.rst[j]);
+      a.yst = double(d.yst[j]);
+      a.bwd = double(d.Bw[cur][j]);
+      a.ds = ineq ? double(d.s[cur][j]) : 0.0;
+      a.dr = double(d.r[cur][j]);
+      a.dyv = double(d.y[cur][j]);
+      row_cand(q, a);
       if (mode == 0) {
         T sa = ineq ? d.sbar[a0][j] : T(0), ra = d.rbar[a0][j], ya = d.ybar[a0][j];
         if (acc) {
@@ -389,29 +428,33 @@ __global__ void __launch_bounds__(kBlock) k_check_rows(Dev<T> d, int mode) {
         }
         const T bwa = axb - sa - ra;
         d.Bwbar[j] = bwa;
-        RowCand<T>::add(q + 8, ineq, bwa, h, sa, ra, ya, lam, sig, ls, us, es, er, dyv, sst, rst, yst);
+        a.bwd = double(bwa);
+        a.ds = double(sa);
+        a.dr = double(ra);
+        a.dyv = double(ya);
+        row_cand(q + 8, a);
       }
     }
   }
   block_reduce_store<16>(q, CK_MAXMASK, d.part + P_CK_R * kMaxBlocks);
 }
 
-template <typename T>
-__device__ __forceinline__ void col_cand(double *q, T x, T hx, T aty, T qx, T lx, T ux, T ex, T xst) {
-  const double g = double(hx) + double(qx) - double(aty);
-  const double xv = double(x), lo = double(lx), hi = double(ux);
-  double p = xv - g;
-  p = p < lo ? lo : p;
-  p = p > hi ? hi : p;
-  q[2] = fmax(q[2], fabs(xv - p));
-  q[3] = fmax(q[3], fmax(fabs(double(hx)), fmax(fabs(double(qx)), fabs(double(aty)))));
-  const double e2 = double(ex) * double(ex);
-  double p2 = xv - e2 * g;
-  p2 = p2 < lo ? lo : p2;
-  p2 = p2 > hi ? hi : p2;
-  const double k = (xv - p2) / double(ex);
+// Contributions of one variable (x block) to the 8 quantities of a candidate:
+// dx, H dx, A' dy corrections plus the base data of the variable.
+__device__ __forceinline__ void col_cand(double *q, double dx, double hdx, double atdy, double qx, double qx0,
+                                         double hxb, double atyb, double lx, double ux, double ex, double xst) {
+  const double g = hdx + qx - atdy;  // gradient of the inner Lagrangian at the point
+  double p = dx - g;
+  p = p < lx ? lx : p;
+  p = p > ux ? ux : p;
+  q[2] = fmax(q[2], fabs(dx - p));
+  q[3] = fmax(q[3], fmax(fabs(hxb + hdx), fmax(fabs(qx0), fabs(atyb + atdy))));
+  double p2 = dx - ex * ex * g;
+  p2 = p2 < lx ? lx : p2;
+  p2 = p2 > ux ? ux : p2;
+  const double k = (dx - p2) / ex;
   q[5] += k * k;
-  const double w = (xv - double(xst)) / double(ex);
+  const double w = (dx - xst) / ex;
   q[6] += w * w;
 }
 
@@ -433,8 +476,11 @@ __global__ void __launch_bounds__(kBlock) k_check_cols(Dev<T> d, int mode) {
       atyb = tile_row_sum<G, T>(d.At.rp, d.At.ci, d.At.val, tile, d.n, [&](int k, T a) { return a * yb[k]; });
     const long long i = tile + ti.lane;
     if (i < d.n) {
-      const T qx = d.qx[i], lx = d.lx[i], ux = d.ux[i], ex = d.ex[i], xst = d.xst[i];
-      col_cand<T>(q, d.x[cur][i], d.Hx[cur][i], d.Aty[cur][i], qx, lx, ux, ex, xst);
+      const double qx = double(d.qx[i]), qx0 = double(d.qx0[i]), hxb = double(d.Hxb[i]);
+      const double atyb0 = double(d.Atyb[i]), lx = double(d.lx[i]), ux = double(d.ux[i]);
+      const double ex = double(d.ex[i]), xst = double(d.xst[i]);
+      col_cand(q, double(d.x[cur][i]), double(d.Hx[cur][i]), double(d.Aty[cur][i]), qx, qx0, hxb, atyb0, lx, ux, ex,
+               xst);
       if (mode == 0) {
         d.Atybar[i] = atyb;
         T xa = d.xbar[a0][i], ha = d.Hxbar[a0][i];
@@ -444,7 +490,7 @@ __global__ void __launch_bounds__(kBlock) k_check_cols(Dev<T> d, int mode) {
           d.xbar[ab][i] = xa;
           d.Hxbar[ab][i] = ha;
         }
-        col_cand<T>(q + 8, xa, ha, atyb, qx, lx, ux, ex, xst);
+        col_cand(q + 8, double(xa), double(ha), double(atyb), qx, qx0, hxb, atyb0, lx, ux, ex, xst);
       }
     }
   }
@@ -564,35 +610,73 @@ __global__ void __launch_bounds__(kBlock) k_check_apply(Dev<T> d) {
 // diagonal steps, cached products.
 // ===========================================================================
 
-// q_x = c - gamma^-1 z (Eq. inner-qp); bounds in T.
+// Base rows of one inner solve (Eq. inner-warm-start, in FP64): v = A x_b,
+// s_b = P_[l_c,u_c](v + lambda / sigma) and r_b = v - s_b on inequality rows,
+// r_b = v - b_E on equality rows; then B w_b, h' = h - B w_b, the base
+// gradients of the s and r blocks, the shifted slack bounds, and zero
+// corrections.
 template <typename T>
-__global__ void k_form_qx(Dev<T> d, const double *c, const double *z, double ginv) {
-  PDNQP_GRID_STRIDE(i, d.n) d.qx[i] = T(c[i] - z[i] * ginv);
+__global__ void __launch_bounds__(kBlock) k_base_rows(Dev<T> d, Mat<double> Ad, const double *lc, const double *uc,
+                                                      double *sb, double *rb) {
+  const int cur = d.st->cur;
+  const double *__restrict__ x = d.xb;
+  PDNQP_GRID_STRIDE(j, d.m) {
+    double v = 0.0;
+    for (int k = Ad.rp[j]; k < Ad.rp[j + 1]; ++k) v += Ad.val[k] * x[Ad.ci[k]];
+    const double lam = d.lam[j], sig = d.sig[j], yb = d.yb[j];
+    double s = 0.0, r, bw;
+    if (j >= d.mE) {
+      s = v + lam / sig;
+      s = s < lc[j] ? lc[j] : s;
+      s = s > uc[j] ? uc[j] : s;
+      r = v - s;
+      bw = v - s - r;
+      d.ls[j] = T(lc[j] - s);
+      d.us[j] = T(uc[j] - s);
+      d.qs[j] = T(yb);
+      d.s[cur][j] = T(0);
+    } else {
+      r = v - lc[j];
+      bw = v - r;
+    }
+    const double h = j < d.mE ? lc[j] : 0.0;
+    sb[j] = s;
+    rb[j] = r;
+    d.h[j] = T(h);
+    d.Bwb[j] = T(bw);
+    d.hp[j] = T(h - bw);
+    d.qr[j] = T(lam + sig * r + yb);
+    d.r[cur][j] = T(0);
+    d.y[cur][j] = T(0);
+    d.Bw[cur][j] = T(0);
+  }
 }
 
-// Eq. inner-warm-start: s = P_[l_c,u_c](A_I x + lambda / sigma), r_E = A_E x - b_E,
-// r_I = A_I x - s, and the cached B w = A x - s - r.
+// Base columns: H x_b and A' y_b in FP64, q'_x = c - z / gamma + H x_b - A' y_b,
+// q_x, the shifted bounds, and zero corrections with zero cached products.
 template <typename T, int G>
-__global__ void __launch_bounds__(kBlock) k_warm_rows(Dev<T> d) {
+__global__ void __launch_bounds__(kBlock) k_base_cols(Dev<T> d, Mat<double> Hd, Mat<double> Atd, const double *c,
+                                                      const double *z, const double *lxd, const double *uxd,
+                                                      double ginv) {
   const int cur = d.st->cur;
-  const T *__restrict__ x = d.x[cur];
+  const double *__restrict__ x = d.xb;
+  const double *__restrict__ y = d.yb;
   TileIter ti;
-  for (long long tile = ti.first; tile < d.m; tile += ti.step) {
-    const T ax = tile_row_sum<G, T>(d.A.rp, d.A.ci, d.A.val, tile, d.m, [&](int k, T a) { return a * x[k]; });
-    const long long j = tile + ti.lane;
-    if (j < d.m) {
-      T r, bw;
-      if (j >= d.mE) {
-        const T s = clampv<T>(T(double(ax) + d.lam[j] / d.sig[j]), d.ls[j], d.us[j]);
-        r = ax - s;
-        d.s[cur][j] = s;
-        bw = ax - s - r;
-      } else {
-        r = ax - d.h[j];
-        bw = ax - r;
-      }
-      d.r[cur][j] = r;
-      d.Bw[cur][j] = bw;
+  for (long long tile = ti.first; tile < d.n; tile += ti.step) {
+    const double hx = tile_row_sum<G, double>(Hd.rp, Hd.ci, Hd.val, tile, d.n, [&](int k, double a) { return a * x[k]; });
+    const double aty = tile_row_sum<G, double>(Atd.rp, Atd.ci, Atd.val, tile, d.n, [&](int k, double a) { return a * y[k]; });
+    const long long i = tile + ti.lane;
+    if (i < d.n) {
+      const double q0 = c[i] - z[i] * ginv;
+      d.qx0[i] = T(q0);
+      d.qx[i] = T(q0 + hx - aty);
+      d.Hxb[i] = T(hx);
+      d.Atyb[i] = T(aty);
+      d.lx[i] = T(lxd[i] - x[i]);
+      d.ux[i] = T(uxd[i] - x[i]);
+      d.x[cur][i] = T(0);
+      d.Hx[cur][i] = T(0);
+      d.Aty[cur][i] = T(0);
     }
   }
 }
@@ -725,24 +809,6 @@ __global__ void __launch_bounds__(kBlock) k_my_rows(Dev<T> d, const double *mwx)
   }
 }
 
-// Cached products of the inner start: H x and A' y.
-template <typename T, int G>
-__global__ void __launch_bounds__(kBlock) k_cache_cols(Dev<T> d) {
-  const int cur = d.st->cur;
-  const T *__restrict__ x = d.x[cur];
-  const T *__restrict__ y = d.y[cur];
-  TileIter ti;
-  for (long long tile = ti.first; tile < d.n; tile += ti.step) {
-    const T hx = tile_row_sum<G, T>(d.H.rp, d.H.ci, d.H.val, tile, d.n, [&](int k, T a) { return a * x[k]; });
-    const T aty = tile_row_sum<G, T>(d.At.rp, d.At.ci, d.At.val, tile, d.n, [&](int k, T a) { return a * y[k]; });
-    const long long i = tile + ti.lane;
-    if (i < d.n) {
-      d.Hx[cur][i] = hx;
-      d.Aty[cur][i] = aty;
-    }
-  }
-}
-
 // Epoch start and averages of the inner start (buffer 0).
 template <typename T>
 __global__ void k_inner_init(Dev<T> d) {
@@ -760,6 +826,38 @@ __global__ void k_inner_init(Dev<T> d) {
     if (j >= d.mE) {
       d.sst[j] = d.s[cur][j];
       d.sbar[0][j] = d.s[cur][j];
+    }
+  }
+}
+
+// End of an inner solve: the outer x and inner y become base + correction
+// (the current point, or the average when it is the converged candidate).
+template <typename T>
+__global__ void k_finish(Dev<T> d, double *x64, double *y64, int use_avg) {
+  const int cur = d.st->cur, ab = d.st->acur ^ d.st->accepted;
+  const T *__restrict__ dx = use_avg ? d.xbar[ab] : d.x[cur];
+  const T *__restrict__ dy = use_avg ? d.ybar[ab] : d.y[cur];
+  PDNQP_GRID_STRIDE(i, d.n) x64[i] += double(dx[i]);
+  PDNQP_GRID_STRIDE(j, d.m) y64[j] += double(dy[j]);
+}
+
+// Totals of the current and averaged points for a snapshot:
+// out = [w (dw) | y (m) | wbar (dw) | ybar (m)], w = (x, s_I, r_E, r_I).
+template <typename T>
+__global__ void k_totals(Dev<T> d, double *out) {
+  const int cur = d.st->cur, ab = d.st->acur ^ d.st->accepted;
+  const long long n = d.n, m = d.m, mI = m - d.mE, dw = n + mI + m;
+  for (int a = 0; a < 2; ++a) {
+    const T *x = a ? d.xbar[ab] : d.x[cur];
+    const T *s = a ? d.sbar[ab] : d.s[cur];
+    const T *r = a ? d.rbar[ab] : d.r[cur];
+    const T *y = a ? d.ybar[ab] : d.y[cur];
+    double *o = out + a * (dw + m);
+    PDNQP_GRID_STRIDE(i, n) o[i] = d.xb[i] + double(x[i]);
+    PDNQP_GRID_STRIDE(j, m) {
+      if (j >= d.mE) o[n + (j - d.mE)] = d.sb[j] + double(s[j]);
+      o[n + mI + j] = d.rb[j] + double(r[j]);
+      o[dw + j] = d.yb[j] + double(y[j]);
     }
   }
 }

@@ -204,27 +204,24 @@ __global__ void k_scale_into(double *dst, const double *src, double a, long long
 // Initial point and penalties (Sec. 3.2.1).
 // ---------------------------------------------------------------------------
 // x = P_[lx,ux](x0 / Dx) (x0 already in the original coordinates, or null).
-template <typename T>
-__global__ void k_init_x(Dev<T> d, const double *x0, const double *Dx, const double *lx, const double *ux,
-                         double *z) {
-  const int cur = d.st->cur;
-  PDNQP_GRID_STRIDE(i, d.n) {
+__global__ void k_init_x(long long n, const double *x0, const double *Dx, const double *lx, const double *ux,
+                         double *x64, double *z) {
+  PDNQP_GRID_STRIDE(i, n) {
     double v = x0 ? x0[i] / Dx[i] : 0.0;
     v = v < lx[i] ? lx[i] : v;
     v = v > ux[i] ? ux[i] : v;
-    d.x[cur][i] = T(v);
-    z[i] = double(T(v));
+    x64[i] = v;
+    z[i] = v;
   }
 }
 
 // lambda (scaled) = c_s lambda0 / Dc (internal row order), inner y = -lambda.
-template <typename T>
-__global__ void k_init_lambda(Dev<T> d, double *lam, const double *lam0_int, const double *Dc, double cs) {
-  const int cur = d.st->cur;
-  PDNQP_GRID_STRIDE(j, d.m) {
+__global__ void k_init_lambda(long long m, double *lam, const double *lam0_int, const double *Dc, double cs,
+                              double *y64) {
+  PDNQP_GRID_STRIDE(j, m) {
     const double l = lam0_int ? cs * lam0_int[j] / Dc[j] : 0.0;
     lam[j] = l;
-    d.y[cur][j] = T(-l);
+    y64[j] = -l;
   }
 }
 
@@ -233,7 +230,7 @@ __global__ void k_init_lambda(Dev<T> d, double *lam, const double *lam0_int, con
 template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_init_rows(Dev<T> d, Mat<double> Ad, const double *lc, const double *uc,
                                                       double *lam, const double *sig, double *rprev, int pass) {
-  const T *__restrict__ x = d.x[d.st->cur];
+  const double *__restrict__ x = d.xb;
   double acc = 0.0;
   GroupIter<G> it;
   for (long long base = it.first; base < d.m; base += it.step) {
@@ -268,7 +265,7 @@ __global__ void __launch_bounds__(kBlock) k_init_rows(Dev<T> d, Mat<double> Ad, 
 // Partials of x'Qx (from H x - gamma^-1 x) and c'x.
 template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_objective(Dev<T> d, Mat<double> Hd, const double *c, double ginv) {
-  const T *__restrict__ x = d.x[d.st->cur];
+  const double *__restrict__ x = d.xb;
   double xqx = 0.0, cx = 0.0;
   GroupIter<G> it;
   for (long long base = it.first; base < d.n; base += it.step) {
@@ -300,7 +297,7 @@ template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_outer_rows(Dev<T> d, Mat<double> Ad, const double *lc, const double *uc,
                                                        const double *Dc, double *lam, const double *sig, double *rcur,
                                                        int update) {
-  const T *__restrict__ x = d.x[d.st->cur];
+  const double *__restrict__ x = d.xb;  // outer x (FP64)
   double q[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) q[k] = 0.0;
@@ -345,7 +342,7 @@ template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_outer_cols(Dev<T> d, Mat<double> Hd, Mat<double> Atd, const double *c,
                                                        const double *lx, const double *ux, const double *Dx,
                                                        const double *lam, const double *z, double ginv, double cs) {
-  const T *__restrict__ x = d.x[d.st->cur];
+  const double *__restrict__ x = d.xb;  // outer x (FP64)
   double q[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) q[k] = 0.0;

@@ -421,21 +421,25 @@ class Solver : public SolverBase {
       PDNQP_CK(cudaMemsetAsync(d.s[b], 0, sizeof(T) * std::max(m_, 1), s_));
       PDNQP_CK(cudaMemsetAsync(d.sbar[b], 0, sizeof(T) * std::max(m_, 1), s_));
     }
-    T **nv[] = {&d.qx, &d.lx, &d.ux, &d.taux, &d.itaux, &d.ex, &d.xst, &d.Atybar};
+    T **nv[] = {&d.qx, &d.qx0, &d.Hxb, &d.Atyb, &d.lx, &d.ux, &d.taux, &d.itaux, &d.ex, &d.xst, &d.Atybar};
     for (T **p : nv) PDNQP_TRY(dalloc(p, n_));
-    T **mv[] = {&d.eta, &d.taus, &d.taur, &d.ieta, &d.itaus, &d.itaur, &d.es, &d.er, &d.dy, &d.h,
-                 &d.ls, &d.us, &d.yst, &d.sst, &d.rst, &d.Bwbar};
+    T **mv[] = {&d.qs, &d.qr, &d.hp, &d.h, &d.Bwb, &d.ls, &d.us, &d.eta, &d.taus, &d.taur, &d.ieta, &d.itaus,
+                &d.itaur, &d.es, &d.er, &d.dy, &d.yst, &d.sst, &d.rst, &d.Bwbar};
     for (T **p : mv) {
       PDNQP_TRY(dalloc(p, m_));
       PDNQP_CK(cudaMemsetAsync(*p, 0, sizeof(T) * std::max(m_, 1), s_));
     }
-    k_to_T<T><<<grid_n(), kBlock, 0, s_>>>(d.lx, lxd_, n_);
-    k_to_T<T><<<grid_n(), kBlock, 0, s_>>>(d.ux, uxd_, n_);
-    if (m_) {
-      k_to_T<T><<<grid_m(), kBlock, 0, s_>>>(d.ls, lcd_, m_);
-      k_to_T<T><<<grid_m(), kBlock, 0, s_>>>(d.us, ucd_, m_);
-      k_form_h<T><<<grid_m(), kBlock, 0, s_>>>(d.h, lcd_, m_, mE_);
-    }
+    PDNQP_TRY(dalloc(&x64_, n_));
+    PDNQP_TRY(dalloc(&y64_, m_));
+    PDNQP_TRY(dalloc(&sb64_, m_));
+    PDNQP_TRY(dalloc(&rb64_, m_));
+    PDNQP_CK(cudaMemsetAsync(sb64_, 0, sizeof(double) * std::max(m_, 1), s_));
+    PDNQP_CK(cudaMemsetAsync(rb64_, 0, sizeof(double) * std::max(m_, 1), s_));
+    PDNQP_CK(cudaMemsetAsync(y64_, 0, sizeof(double) * std::max(m_, 1), s_));
+    d.xb = x64_;
+    d.yb = y64_;
+    d.sb = sb64_;
+    d.rb = rb64_;
     d.lam = lam_;
     d.sig = sig_;
     d.part = part_;
@@ -583,8 +587,8 @@ class Solver : public SolverBase {
     PDNQP_CK(cudaMemcpyAsync(st_, &S, sizeof(S), cudaMemcpyHostToDevice, s_));
     if (has_x0_) PDNQP_CK(cudaMemcpyAsync(dx0_, h_x0_.data(), sizeof(double) * n_, cudaMemcpyHostToDevice, s_));
     if (has_l0_) PDNQP_CK(cudaMemcpyAsync(dl0_, h_l0_.data(), sizeof(double) * m_, cudaMemcpyHostToDevice, s_));
-    k_init_x<T><<<grid_n(), kBlock, 0, s_>>>(d_, has_x0_ ? dx0_ : nullptr, Dx_, lxd_, uxd_, z_);
-    if (m_) k_init_lambda<T><<<grid_m(), kBlock, 0, s_>>>(d_, lam_, has_l0_ ? dl0_ : nullptr, Dc_, cs_);
+    k_init_x<<<grid_n(), kBlock, 0, s_>>>(n_, has_x0_ ? dx0_ : nullptr, Dx_, lxd_, uxd_, x64_, z_);
+    if (m_) k_init_lambda<<<grid_m(), kBlock, 0, s_>>>(m_, lam_, has_l0_ ? dl0_ : nullptr, Dc_, cs_, y64_);
     // f(x0) and the constraint violation for sigma0
     double ob[2];
     {
@@ -621,8 +625,11 @@ class Solver : public SolverBase {
   // a0: setup of one inner solve (Algorithm 4 lines "warm start" and "inner scaling").
   int inner_setup(const Params &prm, double dta, double dtr, long long k_in, long long pause_at, int ignore) {
     const double ginv = 1.0 / gamma_;
-    k_form_qx<T><<<grid_n(), kBlock, 0, s_>>>(d_, c_, z_, ginv);
-    if (m_) with_G(gA_, [&](auto GG) { k_warm_rows<T, decltype(GG)::value><<<nb_rows(), kBlock, 0, s_>>>(d_); });
+    // Base point of this solve (FP64) and zero corrections.
+    if (m_) k_base_rows<T><<<grid_m(), kBlock, 0, s_>>>(d_, Ad_, lcd_, ucd_, sb64_, rb64_);
+    with_G(gN_, [&](auto GG) {
+      k_base_cols<T, decltype(GG)::value><<<nb_cols(), kBlock, 0, s_>>>(d_, Hd_, Atd_, c_, z_, lxd_, uxd_, ginv);
+    });
     k_iscale_init<T><<<grid_nm(), kBlock, 0, s_>>>(d_);
     for (int sw = 0; sw < prm.ruiz_inner; ++sw) {
       with_G(gN_, [&](auto GG) {
@@ -636,7 +643,6 @@ class Solver : public SolverBase {
     }
     with_G(gN_, [&](auto GG) { k_mw_cols<T, decltype(GG)::value><<<nb_cols(), kBlock, 0, s_>>>(d_, scn_[0]); });
     if (m_) with_G(gA_, [&](auto GG) { k_my_rows<T, decltype(GG)::value><<<nb_rows(), kBlock, 0, s_>>>(d_, scn_[0]); });
-    with_G(gN_, [&](auto GG) { k_cache_cols<T, decltype(GG)::value><<<nb_cols(), kBlock, 0, s_>>>(d_); });
     k_inner_init<T><<<grid_nm(), kBlock, 0, s_>>>(d_);
     // Device state of this solve (the host holds every field it needs; the
     // iterates sit in buffer 0 between inner solves).
@@ -717,17 +723,9 @@ class Solver : public SolverBase {
     accepted_ = S.accepted_all;
     restarts_ = S.restarts;
     omega_ = S.omega;
-    const int cur = S.cur;
-    if (cur != 0) {
-      // Keep the outer x / inner y in buffer 0 so the next solve starts there.
-      PDNQP_CK(cudaMemcpyAsync(d_.x[0], d_.x[1], sizeof(T) * n_, cudaMemcpyDeviceToDevice, s_));
-      if (m_) PDNQP_CK(cudaMemcpyAsync(d_.y[0], d_.y[1], sizeof(T) * m_, cudaMemcpyDeviceToDevice, s_));
-    }
-    if (S.status == ST_CONVERGED && S.ret_avg) {
-      const int ab = S.acur ^ S.accepted;
-      PDNQP_CK(cudaMemcpyAsync(d_.x[0], d_.xbar[ab], sizeof(T) * n_, cudaMemcpyDeviceToDevice, s_));
-      if (m_) PDNQP_CK(cudaMemcpyAsync(d_.y[0], d_.ybar[ab], sizeof(T) * m_, cudaMemcpyDeviceToDevice, s_));
-    }
+    // Outer x and inner y = base + correction (current point or converged average).
+    k_finish<T><<<grid_nm(), kBlock, 0, s_>>>(d_, x64_, y64_, (S.status == ST_CONVERGED && S.ret_avg) ? 1 : 0);
+    PDNQP_CK(cudaGetLastError());
     DevState Z = S;
     Z.cur = 0;
     Z.status = ST_IDLE;
@@ -835,7 +833,7 @@ class Solver : public SolverBase {
       dtr = std::max(dtr * rho, prm.tol_floor * er);
       // Eq. center-update / center-tolerance-update.
       if (rps <= eak + erk * sps) {
-        k_copy_to_double<T><<<grid_n(), kBlock, 0, s_>>>(z_, d_.x[0], n_);
+        PDNQP_CK(cudaMemcpyAsync(z_, x64_, sizeof(double) * n_, cudaMemcpyDeviceToDevice, s_));
         eak = std::max(eak * prm.rho_z, ea);
         erk = std::max(erk * prm.rho_z, er);
       }
@@ -843,7 +841,7 @@ class Solver : public SolverBase {
     }
     // Result in the original coordinates.
     PDNQP_TRY(outer_residuals(0, q));
-    k_unscale<T><<<grid_nm(), kBlock, 0, s_>>>(d_.x[0], Dx_, n_, lam_, Dc_, m_, cs_, xo_, lo_);
+    k_unscale<double><<<grid_nm(), kBlock, 0, s_>>>(x64_, Dx_, n_, lam_, Dc_, m_, cs_, xo_, lo_);
     PDNQP_CK(cudaGetLastError());
     PDNQP_CK(cudaStreamSynchronize(s_));
     res_.status = status;
@@ -878,24 +876,11 @@ class Solver : public SolverBase {
 
   int snapshot(const DevState &S, double *o) {
     const long long n = n_, m = m_, mI = m_ - mE_, dw = n + mI + m;
-    const int cur = S.cur, ab = S.acur ^ S.accepted;
-    std::vector<T> tx(std::max(n, m));
-    auto put = [&](const T *src, long long cnt, long long off, long long src_off) -> int {
-      if (cnt == 0) return 0;
-      PDNQP_CK(cudaMemcpyAsync(tx.data(), src + src_off, sizeof(T) * cnt, cudaMemcpyDeviceToHost, s_));
-      PDNQP_CK(cudaStreamSynchronize(s_));
-      for (long long i = 0; i < cnt; ++i) o[off + i] = double(tx[i]);
-      return 0;
-    };
-    // w = (x, s_I, r_E, r_I); s rows mE..m-1 hold s_I, r rows are E then I.
-    PDNQP_TRY(put(d_.x[cur], n, 0, 0));
-    PDNQP_TRY(put(d_.s[cur], mI, n, mE_));
-    PDNQP_TRY(put(d_.r[cur], m, n + mI, 0));
-    PDNQP_TRY(put(d_.y[cur], m, dw, 0));
-    PDNQP_TRY(put(d_.xbar[ab], n, dw + m, 0));
-    PDNQP_TRY(put(d_.sbar[ab], mI, dw + m + n, mE_));
-    PDNQP_TRY(put(d_.rbar[ab], m, dw + m + n + mI, 0));
-    PDNQP_TRY(put(d_.ybar[ab], m, 2 * dw + m, 0));
+    if (!snapbuf_) PDNQP_TRY(dalloc(&snapbuf_, (size_t)(2 * (dw + m))));
+    k_totals<T><<<grid_nm(), kBlock, 0, s_>>>(d_, snapbuf_);
+    PDNQP_CK(cudaGetLastError());
+    PDNQP_CK(cudaMemcpyAsync(o, snapbuf_, sizeof(double) * 2 * (dw + m), cudaMemcpyDeviceToHost, s_));
+    PDNQP_CK(cudaStreamSynchronize(s_));
     double *sc = o + 2 * (dw + m);
     sc[0] = S.omega;
     sc[1] = S.kappa;
@@ -955,6 +940,7 @@ class Solver : public SolverBase {
   double *c_ = nullptr, *lxd_ = nullptr, *uxd_ = nullptr, *lcd_ = nullptr, *ucd_ = nullptr;
   double *Dc_ = nullptr, *Dx_ = nullptr, *lam_ = nullptr, *sig_ = nullptr, *rprev_ = nullptr, *rcur_ = nullptr;
   double *z_ = nullptr, *xo_ = nullptr, *lo_ = nullptr, *dx0_ = nullptr, *dl0_ = nullptr;
+  double *x64_ = nullptr, *y64_ = nullptr, *sb64_ = nullptr, *rb64_ = nullptr, *snapbuf_ = nullptr;
   double *scn_[2] = {nullptr, nullptr}, *scm_[3] = {nullptr, nullptr, nullptr};
   double *V_ = nullptr, *hdev_ = nullptr, *lzpart_ = nullptr;
   double *part_ = nullptr, *dred_ = nullptr;

@@ -1,0 +1,65 @@
+"""FP32-bulk form (SpMVs and vector updates in FP32, FP64 acceptance sums,
+check/restart/termination reductions, multiplier and penalty updates, base
+point): error against the FP64 oracle, and end-to-end KKT acceptance."""
+import numpy as np
+import pytest
+
+from paper_2609_19557_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2609_19557_gb300 import build as B
+    from paper_2609_19557_gb300 import pdnqp
+    B.build()
+    pdnqp.load()
+    return pdnqp
+
+
+def rel_err(a, b):
+    return np.abs(a - b).max(initial=0.0) / max(np.abs(b).max(initial=0.0), 1e-300)
+
+
+def test_fp32_iterates_track_fp64_oracle(P, oracle):
+    """Stated error of the FP32-bulk iterates vs the FP64 oracle over the first
+    200 iterations of the first inner solve (n=200 workload): below 1e-4 relative."""
+    inst = I.small_qp(0)
+    ck = [1, 10, 50, 100, 200]
+    h = P.create_from_instance(inst, precision=P.PDNQP_FP32_BULK)
+    gpu = P.pdnqp_debug_inner(h, ck)
+    ref, _ = oracle.debug_inner(inst, ck)
+    errs = []
+    for s, r in zip(gpu, ref):
+        assert s["t_total"] == r["t_total"]
+        e = max(rel_err(s[k], r[k]) for k in ("w", "y", "wbar", "ybar"))
+        errs.append(e)
+    print("fp32 vs oracle rel err at", ck, ":", ["%.2e" % e for e in errs])
+    assert max(errs) < 1e-4
+    h.close()
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6])
+def test_fp32_end_to_end_small(P, oracle, eps):
+    inst = I.small_qp(0)
+    h = P.create_from_instance(inst, precision=P.PDNQP_FP32_BULK)
+    P.pdnqp_set_param(h, "time_limit", 120)
+    st = P.pdnqp_solve(h, eps, eps)
+    x, y, res = P.pdnqp_get(h)
+    assert st == P.PDNQP_SOLVED, (P.STATUS_NAMES[st], res)
+    assert oracle.kkt_pass(inst, x, y, eps, eps)
+    h.close()
+
+
+def test_fp32_end_to_end_mid(P, oracle):
+    inst = I.mid_qp(0)
+    h = P.create_from_instance(inst, precision=P.PDNQP_FP32_BULK)
+    P.pdnqp_set_param(h, "time_limit", 300)
+    st = P.pdnqp_solve(h, 1e-4, 1e-4)
+    x, y, res = P.pdnqp_get(h)
+    assert st == P.PDNQP_SOLVED, (P.STATUS_NAMES[st], res)
+    assert oracle.kkt_pass(inst, x, y, 1e-4, 1e-4)
+    h.close()
