@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--ttk", type=float, default=0.0, help="also time a solve to rel-KKT 1e-4 (cap in seconds)")
     p.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU (oracle) baseline leg")
+    p.add_argument("--graph", default="cond", choices=["cond", "unrolled"],
+                   help="inner loop as a conditional (WHILE/IF) graph, or unrolled slots (inspectable by ncu)")
     p.add_argument("--n", type=int, default=1_000_000)
     p.add_argument("--m", type=int, default=500_000)
     return p.parse_args()
@@ -140,6 +142,7 @@ def run_native(args):
     stream = torch.cuda.current_stream()
     h = P.create_from_instance(inst, precision=args.precision, stream=stream.cuda_stream)
     P.pdnqp_set_param(h, "iter_budget", args.budget)
+    P.pdnqp_set_param(h, "cond_graph", 1 if args.graph == "cond" else 0)
 
     def barrier():
         if ws > 1:

@@ -149,8 +149,11 @@ PDNQP_API int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0);
  * delta_sigma, sigma_max, tol_floor, gamma (override, > 0; setting it
  * replaces the Lanczos choice), chunk (trial slots per CUDA-graph launch),
  * iter_budget (cap on accepted inner iterations per pdnqp_solve, summed over
- * outer iterations; ITER_LIMIT when reached), g_rows / g_cols (lanes per CSR
- * row in the SpMV kernels, 0 = from the mean row length).
+ * outer iterations; ITER_LIMIT when reached), g_rows / g_cols (nonzeros per
+ * lane per CSR-stream chunk in the row / column SpMV kernels: 4, 8 or 16; 0 =
+ * from the mean row length), cond_graph (1: inner loop as a device-driven
+ * CUDA graph with conditional WHILE/IF nodes; 0: unrolled graph of `chunk`
+ * trial slots, which profilers can inspect kernel by kernel).
  * Returns PDNQP_ERR_ARG for an unknown name or an out-of-range value. */
 PDNQP_API int pdnqp_set_param(pdnqp_t *h, const char *name, double value);
 PDNQP_API int pdnqp_get_param(const pdnqp_t *h, const char *name, double *value);
@@ -175,10 +178,14 @@ PDNQP_API const char *pdnqp_last_error(const pdnqp_t *h);
 PDNQP_API int pdnqp_debug_inner(pdnqp_t *h, int n_ckpt, const int64_t *ckpt, double *snap);
 
 /* Measurement hook: replays one hot-path kernel `reps` times on the handle's
- * stream with the state left by the last solve (which = 0: the fused Q/A^T
- * SpMV + acceptance kernel, 1: the fused A SpMV + dual-step kernel, 2: the
- * primal step).  The replays write only trial buffers.  Returns 0 or an error. */
+ * stream with the state left by the last solve (which & 7 = 0: the fused
+ * Q/A^T SpMV + acceptance kernel, 1: the fused A SpMV + dual-step kernel, 2:
+ * the primal step).  With which | 8 the launches are captured into one CUDA
+ * graph, launched once and timed with CUDA events (pdnqp_replay_last_ms).
+ * The replays write only trial buffers and the device state is restored.
+ * Returns 0 or an error. */
 PDNQP_API int pdnqp_replay_kernel(pdnqp_t *h, int which, int reps);
+PDNQP_API double pdnqp_replay_last_ms(const pdnqp_t *h);
 
 /* Algorithmic (compulsory) DRAM bytes of one launch of the kernel `which`
  * (same numbering as pdnqp_replay_kernel) and of one accepted iteration

@@ -361,7 +361,7 @@ int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0) {
   X(beta_suff, d, 0.0, 1.0) X(beta_nec, d, 0.0, 1.0) X(beta_art, d, 0.0, 1.0)                      \
   X(rej_limit, i, 1.0, 1e9) X(kappa_shrink, d, 1e-6, 0.999999) X(delta_sigma, d, 1.0, 1e300)       \
   X(sigma_max, d, 1e-300, 1e300) X(tol_floor, d, 0.0, 1.0) X(chunk, i, 1.0, 65536.0)               \
-  X(g_rows, i, 0.0, 16.0) X(g_cols, i, 0.0, 16.0) X(iter_budget, ll, 1.0, 4e18)
+  X(g_rows, i, 0.0, 16.0) X(g_cols, i, 0.0, 16.0) X(iter_budget, ll, 1.0, 4e18) X(cond_graph, i, 0.0, 1.0)
 
 int pdnqp_set_param(pdnqp_t *h, const char *name, double value) {
   if (!h || !name) return fail(h, PDNQP_ERR_ARG, "NULL handle or name");
@@ -432,12 +432,15 @@ int pdnqp_debug_inner(pdnqp_t *h, int n_ckpt, const int64_t *ckpt, double *snap)
 }
 
 int pdnqp_replay_kernel(pdnqp_t *h, int which, int reps) {
-  if (!h || which < 0 || which > 2 || reps < 0) return fail(h, PDNQP_ERR_ARG, "bad arguments");
+  const int kind = which & 7;
+  if (!h || kind > 2 || (which & ~15) || reps < 0) return fail(h, PDNQP_ERR_ARG, "bad arguments");
   cudaSetDevice(h->device);
   int rc = h->solver->replay(which, reps);
   if (rc < 0) return fail(h, rc, "replay failed (solve first)");
   return 0;
 }
+
+double pdnqp_replay_last_ms(const pdnqp_t *h) { return h ? h->solver->last_replay_ms() : -1.0; }
 
 int pdnqp_kernel_bytes(const pdnqp_t *h, int which, double *bytes) {
   if (!h || !bytes || which < -1 || which > 3) return fail(nullptr, PDNQP_ERR_ARG, "bad arguments");

@@ -79,54 +79,80 @@ __device__ __forceinline__ A group_max(A v) {
   return v;
 }
 
-// Block reduction of NQ doubles; kind[q] = 0 sum, 1 max.  Thread 0 writes
+// Block reduction of NQ doubles; bit q of kind_mask: 0 sum, 1 max (all maxima
+// are of non-negative values).  Thread 0... of the block writes
 // part[q * kMaxBlocks + blockIdx.x].  Must be called by every thread of the
-// block (kBlock threads).  Fixed order: deterministic for a fixed grid.
+// block (kBlock threads).  On this GPU the FP64 pipe is narrow and its cost is
+// per active lane, so the reduction avoids FP64 shuffle trees: values go to
+// shared memory and 8 threads per quantity sum 32 values each serially, then
+// one thread sums the 8.  Fixed order: deterministic for a fixed grid.
 template <int NQ>
 __device__ __forceinline__ void block_reduce_store(double (&v)[NQ], const unsigned kind_mask, double *part) {
-  __shared__ double sm[NQ][kBlock / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int NW = kBlock / 32;
+  constexpr int WIN = 4;  // quantities staged at a time (8 KB of shared memory)
+  __shared__ double sm[WIN][kBlock];
+  __shared__ double s2[WIN][NW];
+  const int t = threadIdx.x;
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    double a = ((kind_mask >> q) & 1u) ? warp_max(v[q]) : warp_sum(v[q]);
-    if (lane == 0) sm[q][wid] = a;
-  }
-  __syncthreads();
-  if (wid == 0) {
+  for (int q0 = 0; q0 < NQ; q0 += WIN) {
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      const bool mx = (kind_mask >> q) & 1u;
-      double a = lane < kBlock / 32 ? sm[q][lane] : (mx ? 0.0 : 0.0);
-      a = mx ? warp_max(a) : warp_sum(a);
-      if (lane == 0) part[q * kMaxBlocks + blockIdx.x] = a;
+    for (int k = 0; k < WIN; ++k)
+      if (q0 + k < NQ) sm[k][t] = v[q0 + k];
+    __syncthreads();
+    if (t < WIN * NW) {
+      const int k = t / NW, c = t % NW, q = q0 + k;
+      if (q < NQ) {
+        const bool mx = (kind_mask >> q) & 1u;
+        const double *src = &sm[k][c * 32];
+        double a = src[0];
+        if (mx) {
+          for (int i = 1; i < 32; ++i) a = fmax(a, src[i]);
+        } else {
+          for (int i = 1; i < 32; ++i) a += src[i];
+        }
+        s2[k][c] = a;
+      }
     }
+    __syncthreads();
+    if (t < WIN && q0 + t < NQ) {
+      const int q = q0 + t;
+      const bool mx = (kind_mask >> q) & 1u;
+      double a = s2[t][0];
+      for (int c = 1; c < NW; ++c) a = mx ? fmax(a, s2[t][c]) : a + s2[t][c];
+      part[q * kMaxBlocks + blockIdx.x] = a;
+    }
+    __syncthreads();
   }
 }
 
-// Single-block final reduction of NQ quantities over nb partials (fixed order).
+// Single-block final reduction of NQ quantities over nb partials (fixed order):
+// warp w handles quantities w, w + nwarps, ...; lane l sums partials l, l + 32,
+// ... serially, then lane 0 combines the 32 lane sums in order.  Every thread
+// of the block gets out[].  blockDim.x must be a multiple of 32.
 template <int NQ>
 __device__ __forceinline__ void final_reduce(const double *part, int nb, const unsigned kind_mask, double (&out)[NQ]) {
-  __shared__ double sm[NQ][kRedThreads / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) {
+  __shared__ double lane_sum[NQ][32];
+  __shared__ double res[NQ];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int q = wid; q < NQ; q += nw) {
     const bool mx = (kind_mask >> q) & 1u;
     double a = 0.0;
-    for (int b = threadIdx.x; b < nb; b += kRedThreads) {
-      double p = part[q * kMaxBlocks + b];
+    for (int b = lane; b < nb; b += 32) {
+      const double p = part[q * kMaxBlocks + b];
       a = mx ? fmax(a, p) : a + p;
     }
-    a = mx ? warp_max(a) : warp_sum(a);
-    if (lane == 0) sm[q][wid] = a;
+    lane_sum[q][lane] = a;
+    __syncwarp();
+    if (lane == 0) {
+      double r = lane_sum[q][0];
+      for (int k = 1; k < 32; ++k) r = mx ? fmax(r, lane_sum[q][k]) : r + lane_sum[q][k];
+      res[q] = r;
+    }
+    __syncwarp();
   }
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    const bool mx = (kind_mask >> q) & 1u;
-    double a = lane < kRedThreads / 32 ? sm[q][lane] : 0.0;
-    a = mx ? warp_max(a) : warp_sum(a);
-    out[q] = __shfl_sync(0xffffffffu, a, 0);
-  }
+  for (int q = 0; q < NQ; ++q) out[q] = res[q];
   __syncthreads();
 }
 

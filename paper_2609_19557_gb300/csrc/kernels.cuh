@@ -70,6 +70,8 @@ struct Dev {
   const double *lam, *sig;          // multipliers and row penalties
   double *part;
   DevState *st;
+  unsigned *ctr;   // arrival counters of the last-block reductions (reset by the last block)
+  cudaGraphConditionalHandle hw, hc;  // device-loop handles (0 when the graph has none)
 };
 
 template <typename T>
@@ -91,6 +93,54 @@ struct SumT {
 #define PDNQP_GRID_STRIDE(i, N) \
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)(N); \
        i += (long long)gridDim.x * blockDim.x)
+
+// The single-block kernels work on a shared-memory copy of the device state
+// (one coalesced load and store) instead of chains of dependent global
+// read-modify-writes.
+__device__ __forceinline__ void state_load(DevState &S, const DevState *g) {
+  for (int i = threadIdx.x; i < (int)(sizeof(DevState) / 4); i += blockDim.x) ((int *)&S)[i] = ((const int *)g)[i];
+  __syncthreads();
+}
+__device__ __forceinline__ void state_store(DevState *g, const DevState &S) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < (int)(sizeof(DevState) / 4); i += blockDim.x) ((int *)g)[i] = ((const int *)&S)[i];
+}
+
+// Start of one graph launch: at most `chunk` trials before control returns to
+// the host.
+__global__ void k_loop_begin(DevState *st, long long chunk) { st->slot_left = chunk; }
+
+// Last-block detection: after this block's partial sums are stored, returns
+// true in the single block that arrives last (its threads then see every
+// block's partials); that block resets the counter at the end of its work.
+__device__ __forceinline__ bool arrive_last(unsigned *ctr) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ctr, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// A kernel that finds the loop stopped ends the device loop (block 0 only).
+// COND = false builds kernels without conditional-handle calls (for unrolled
+// graphs, which profilers can inspect).
+template <bool COND>
+__device__ __forceinline__ void stop_loop(cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hc) {
+  if (COND && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (hw) cudaGraphSetConditional(hw, 0u);
+    if (hc) cudaGraphSetConditional(hc, 0u);
+  }
+}
+
+template <bool COND>
+__device__ void decide_body(DevState *stg, const double *part, int nb_r, int nb_c, cudaGraphConditionalHandle hw,
+                            cudaGraphConditionalHandle hc);
+template <bool COND>
+__device__ void check_final_body(DevState *stg, const double *part, int nb_r, int nb_c,
+                                 cudaGraphConditionalHandle hw);
+__device__ void inner_begin_body(DevState *st, const double *part, int nb_r, int nb_c);
 
 // ===========================================================================
 // Trial step (Eq. pdqp-trial) and acceptance test (Eq. adaptive-condition).
@@ -191,10 +241,13 @@ __global__ void __launch_bounds__(kBlock) k_rows(Dev<T> d) {
 
 // Variable rows: (H x_tr)_i and (A' y_tr)_i (the products with Q and A^T),
 // plus the x terms of the acceptance sums.
-template <typename T, int G>
-__global__ void __launch_bounds__(kBlock) k_cols(Dev<T> d) {
+template <typename T, int G, bool COND>
+__global__ void __launch_bounds__(kBlock) k_cols(Dev<T> d, int nb_r) {
   const DevState *st = d.st;
-  if (st->status != ST_RUNNING) return;
+  if (st->status != ST_RUNNING) {
+    stop_loop<COND>(d.hw, d.hc);
+    return;
+  }
   const int cur = st->cur, nx = 1 - cur;
   const T *__restrict__ xt = d.x[nx];
   const T *__restrict__ yt = d.y[nx];
@@ -217,41 +270,27 @@ __global__ void __launch_bounds__(kBlock) k_cols(Dev<T> d) {
   }
   double v[4] = {double(Lt), 0.0, double(RH), double(RB)};
   block_reduce_store<4>(v, 0u, d.part + P_TR_C * kMaxBlocks);
+  if (arrive_last(d.ctr)) {
+    decide_body<COND>(d.st, d.part, nb_r, gridDim.x, d.hw, d.hc);
+    if (threadIdx.x == 0) d.ctr[0] = 0u;
+  }
 }
 
 // Acceptance decision (single block, deterministic order).  On acceptance the
 // trial buffers become current (index flip); on rejection both step vectors
 // are shrunk through kappa.
-// The single-block kernels work on a shared-memory copy of the device state
-// (one coalesced load and store) instead of chains of dependent global
-// read-modify-writes.
-__device__ __forceinline__ void state_load(DevState &S, const DevState *g) {
-  for (int i = threadIdx.x; i < (int)(sizeof(DevState) / 4); i += blockDim.x) ((int *)&S)[i] = ((const int *)g)[i];
-  __syncthreads();
-}
-__device__ __forceinline__ void state_store(DevState *g, const DevState &S) {
-  __syncthreads();
-  for (int i = threadIdx.x; i < (int)(sizeof(DevState) / 4); i += blockDim.x) ((int *)g)[i] = ((const int *)&S)[i];
-}
 
-// Start of one graph launch: at most `chunk` trials before control returns to
-// the host.
-__global__ void k_loop_begin(DevState *st, long long chunk) { st->slot_left = chunk; }
-
-// hw / hc: conditional handles of the device loop (WHILE over trial slots) and
-// of the periodic check (IF); 0 when the graph has no conditional nodes.
-__global__ void __launch_bounds__(kRedThreads) k_decide(DevState *stg, const double *part, int nb_r, int nb_c,
-                                                        cudaGraphConditionalHandle hw,
-                                                        cudaGraphConditionalHandle hc) {
+// Acceptance decision (Eq. adaptive-condition), run by the last block of the
+// column kernel once every block's partial sums are visible: FP64 sums in a
+// fixed order; on acceptance the trial buffers become current (index flip), on
+// rejection both step vectors shrink through kappa.  Sets the device-loop
+// handles: hw (continue while running and the launch has trials left) and hc
+// (a periodic check follows).
+template <bool COND>
+__device__ void decide_body(DevState *stg, const double *part, int nb_r, int nb_c, cudaGraphConditionalHandle hw,
+                            cudaGraphConditionalHandle hc) {
   __shared__ DevState S;
   state_load(S, stg);
-  if (S.status != ST_RUNNING) {
-    if (threadIdx.x == 0) {
-      if (hw) cudaGraphSetConditional(hw, 0);
-      if (hc) cudaGraphSetConditional(hc, 0);
-    }
-    return;
-  }
   double a[4], b[4];
   final_reduce<4>(part + P_TR_R * kMaxBlocks, nb_r, 0u, a);
   final_reduce<4>(part + P_TR_C * kMaxBlocks, nb_c, 0u, b);
@@ -285,9 +324,11 @@ __global__ void __launch_bounds__(kRedThreads) k_decide(DevState *stg, const dou
       if (st->rej >= st->rej_limit) st->status = ST_NUMERICAL_ERROR;
     }
     st->slot_left -= 1;
-    const bool run = st->status == ST_RUNNING;
-    if (hw) cudaGraphSetConditional(hw, (run && st->slot_left > 0) ? 1u : 0u);
-    if (hc) cudaGraphSetConditional(hc, (run && st->check_due) ? 1u : 0u);
+    if (COND) {
+      const bool run = st->status == ST_RUNNING;
+      if (hw) cudaGraphSetConditional(hw, (run && st->slot_left > 0) ? 1u : 0u);
+      if (hc) cudaGraphSetConditional(hc, (run && st->check_due) ? 1u : 0u);
+    }
   }
   state_store(stg, S);
 }
@@ -458,8 +499,8 @@ __device__ __forceinline__ void col_cand(double *q, double dx, double hdx, doubl
   q[6] += w * w;
 }
 
-template <typename T, int G>
-__global__ void __launch_bounds__(kBlock) k_check_cols(Dev<T> d, int mode) {
+template <typename T, int G, bool COND>
+__global__ void __launch_bounds__(kBlock) k_check_cols(Dev<T> d, int mode, int nb_r) {
   const DevState *st = d.st;
   if (mode == 0 && !(st->status == ST_RUNNING && st->check_due)) return;
   // y bar of a pending acceptance was materialised by k_check_rows.
@@ -495,15 +536,22 @@ __global__ void __launch_bounds__(kBlock) k_check_cols(Dev<T> d, int mode) {
     }
   }
   block_reduce_store<16>(q, CK_MAXMASK, d.part + P_CK_C * kMaxBlocks);
+  if (arrive_last(d.ctr + 1)) {
+    if (mode == 0)
+      check_final_body<COND>(d.st, d.part, nb_r, gridDim.x, d.hw);
+    else
+      inner_begin_body(d.st, d.part, nb_r, gridDim.x);
+    if (threadIdx.x == 0) d.ctr[1] = 0u;
+  }
 }
 
 // Decisions of the check (single block): inner termination of both candidates
 // (Eq. inner-termination), iteration limit, restart criteria and primal weight.
-__global__ void __launch_bounds__(kRedThreads) k_check_final(DevState *stg, const double *part, int nb_r, int nb_c,
-                                                             cudaGraphConditionalHandle hw) {
+template <bool COND>
+__device__ void check_final_body(DevState *stg, const double *part, int nb_r, int nb_c,
+                                 cudaGraphConditionalHandle hw) {
   __shared__ DevState S;
   state_load(S, stg);
-  if (!(S.status == ST_RUNNING && S.check_due)) return;
   double a[16], b[16];
   final_reduce<16>(part + P_CK_R * kMaxBlocks, nb_r, CK_MAXMASK, a);
   final_reduce<16>(part + P_CK_C * kMaxBlocks, nb_c, CK_MAXMASK, b);
@@ -553,7 +601,7 @@ __global__ void __launch_bounds__(kRedThreads) k_check_final(DevState *stg, cons
       }
       if (st->t_total == st->pause_at) st->status = ST_PAUSED;
     }
-    if (hw) cudaGraphSetConditional(hw, (st->status == ST_RUNNING && st->slot_left > 0) ? 1u : 0u);
+    if (COND && hw) cudaGraphSetConditional(hw, (st->status == ST_RUNNING && st->slot_left > 0) ? 1u : 0u);
   }
   state_store(stg, S);
 }
@@ -692,19 +740,21 @@ __global__ void k_iscale_init(Dev<T> d) {
   }
 }
 
+// Reciprocal square root in the storage precision.
+__device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
+
 // Inner Ruiz, l_inf norms of the x columns of [[H~, B~^T], [B~, 0]]:
-// max(max_k |e_k H_ki e_i|, max_j |d_j A_ji e_i|).
+// max(max_k |e_k H_ki e_i|, max_j |d_j A_ji e_i|), in the storage precision T.
 template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_iruiz_cols(Dev<T> d, double *cnx) {
   TileIter ti;
   for (long long tile = ti.first; tile < d.n; tile += ti.step) {
     const long long i = tile + ti.lane;
     // e_i is applied after the reduction (max over k of |e_k H_ki| times e_i).
-    const double a = tile_row_max<G, double>(d.H.rp, d.H.ci, d.H.val, tile, d.n,
-                                             [&](int k, T v) { return fabs(double(d.ex[k]) * double(v)); });
-    const double b = tile_row_max<G, double>(d.At.rp, d.At.ci, d.At.val, tile, d.n,
-                                             [&](int k, T v) { return fabs(double(d.dy[k]) * double(v)); });
-    if (i < d.n) cnx[i] = fmax(a, b) * double(d.ex[i]);
+    const T a = tile_row_max<G, T>(d.H.rp, d.H.ci, d.H.val, tile, d.n, [&](int k, T v) { return fabs(d.ex[k] * v); });
+    const T b = tile_row_max<G, T>(d.At.rp, d.At.ci, d.At.val, tile, d.n, [&](int k, T v) { return fabs(d.dy[k] * v); });
+    if (i < d.n) cnx[i] = double(fmax(a, b) * d.ex[i]);
   }
 }
 
@@ -714,20 +764,19 @@ template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_iruiz_rows(Dev<T> d, double *rn, double *cns, double *cnr) {
   TileIter ti;
   for (long long tile = ti.first; tile < d.m; tile += ti.step) {
-    const double a = tile_row_max<G, double>(d.A.rp, d.A.ci, d.A.val, tile, d.m,
-                                             [&](int k, T v) { return fabs(double(v) * double(d.ex[k])); });
+    const T a = tile_row_max<G, T>(d.A.rp, d.A.ci, d.A.val, tile, d.m, [&](int k, T v) { return fabs(v * d.ex[k]); });
     const long long j = tile + ti.lane;
     if (j < d.m) {
-      const double dj = double(d.dy[j]);
-      const double er = double(d.er[j]);
-      double rowv = fmax(a * dj, dj * er);
+      const T dj = d.dy[j];
+      const T er = d.er[j];
+      T rowv = fmax(a * dj, dj * er);
       if (j >= d.mE) {
-        const double es = double(d.es[j]);
+        const T es = d.es[j];
         rowv = fmax(rowv, dj * es);
-        cns[j] = dj * es;
+        cns[j] = double(dj * es);
       }
-      rn[j] = rowv;
-      cnr[j] = fmax(er * er * d.sig[j], dj * er);
+      rn[j] = double(rowv);
+      cnr[j] = double(fmax(er * er * T(d.sig[j]), dj * er));
     }
   }
 }
@@ -735,42 +784,41 @@ __global__ void __launch_bounds__(kBlock) k_iruiz_rows(Dev<T> d, double *rn, dou
 template <typename T>
 __global__ void k_iruiz_update(Dev<T> d, const double *cnx, const double *rn, const double *cns, const double *cnr) {
   PDNQP_GRID_STRIDE(i, d.n) {
-    const double c = cnx[i];
-    if (c > 0.0) d.ex[i] = T(double(d.ex[i]) * (1.0 / sqrt(c)));
+    const T c = T(cnx[i]);
+    if (c > T(0)) d.ex[i] = d.ex[i] * rsqrt_t(c);
   }
   PDNQP_GRID_STRIDE(j, d.m) {
-    const double r = rn[j];
-    if (r > 0.0) d.dy[j] = T(double(d.dy[j]) * (1.0 / sqrt(r)));
-    const double cr = cnr[j];
-    if (cr > 0.0) d.er[j] = T(double(d.er[j]) * (1.0 / sqrt(cr)));
+    const T r = T(rn[j]);
+    if (r > T(0)) d.dy[j] = d.dy[j] * rsqrt_t(r);
+    const T cr = T(cnr[j]);
+    if (cr > T(0)) d.er[j] = d.er[j] * rsqrt_t(cr);
     if (j >= d.mE) {
-      const double cs = cns[j];
-      if (cs > 0.0) d.es[j] = T(double(d.es[j]) * (1.0 / sqrt(cs)));
+      const T cs = T(cns[j]);
+      if (cs > T(0)) d.es[j] = d.es[j] * rsqrt_t(cs);
     }
   }
 }
 
 // Eq. diagonal-scales for the x columns (m_w) and the effective primal step
-// tau_eff / (kappa / omega) = e^2 * 0.99 / m_w (Eq. diagonal-steps).
+// tau_eff / (kappa / omega) = e^2 * 0.99 / m_w (Eq. diagonal-steps), in the
+// storage precision; imwx = 1 / m_w is kept for m_y.
 template <typename T, int G>
-__global__ void __launch_bounds__(kBlock) k_mw_cols(Dev<T> d, double *mwx) {
+__global__ void __launch_bounds__(kBlock) k_mw_cols(Dev<T> d, double *imwx) {
   TileIter ti;
   for (long long tile = ti.first; tile < d.n; tile += ti.step) {
-    const double h1 = tile_row_sum<G, double>(d.H.rp, d.H.ci, d.H.val, tile, d.n,
-                                              [&](int k, T v) { return fabs(double(d.ex[k]) * double(v)); });
-    const double b1 = tile_row_sum<G, double>(d.At.rp, d.At.ci, d.At.val, tile, d.n,
-                                              [&](int k, T v) { return fabs(double(d.dy[k]) * double(v)); });
-    const double b2 = tile_row_sum<G, double>(d.At.rp, d.At.ci, d.At.val, tile, d.n, [&](int k, T v) {
-      const double bb = double(d.dy[k]) * double(v);
-      return d.sig[k] * bb * bb;
+    const T h1 = tile_row_sum<G, T>(d.H.rp, d.H.ci, d.H.val, tile, d.n, [&](int k, T v) { return fabs(d.ex[k] * v); });
+    const T b1 = tile_row_sum<G, T>(d.At.rp, d.At.ci, d.At.val, tile, d.n, [&](int k, T v) { return fabs(d.dy[k] * v); });
+    const T b2 = tile_row_sum<G, T>(d.At.rp, d.At.ci, d.At.val, tile, d.n, [&](int k, T v) {
+      const T bb = d.dy[k] * v;
+      return T(d.sig[k]) * bb * bb;
     });
     const long long i = tile + ti.lane;
     if (i < d.n) {
-      const double ei = double(d.ex[i]);
-      const double mw = h1 * ei + fmax(b1 * ei, sqrt(b2) * ei);
-      mwx[i] = mw;
-      d.taux[i] = T(ei * ei * (0.99 / mw));
-      d.itaux[i] = T(mw / (0.99 * ei * ei));
+      const T ei = d.ex[i];
+      const T mw = h1 * ei + fmax(b1 * ei, sqrt(b2) * ei);
+      imwx[i] = double(T(1) / mw);
+      d.taux[i] = ei * ei * (T(0.99) / mw);
+      d.itaux[i] = mw / (T(0.99) * ei * ei);
     }
   }
 }
@@ -778,33 +826,33 @@ __global__ void __launch_bounds__(kBlock) k_mw_cols(Dev<T> d, double *mwx) {
 // m_w of the s and r columns, their steps, and m_y with the dual step
 // eta_eff / (kappa omega) = d^2 * 0.99 / m_y.
 template <typename T, int G>
-__global__ void __launch_bounds__(kBlock) k_my_rows(Dev<T> d, const double *mwx) {
+__global__ void __launch_bounds__(kBlock) k_my_rows(Dev<T> d, const double *imwx) {
   TileIter ti;
   for (long long tile = ti.first; tile < d.m; tile += ti.step) {
-    const double a = tile_row_sum<G, double>(d.A.rp, d.A.ci, d.A.val, tile, d.m, [&](int k, T v) {
-      const double bb = double(v) * double(d.ex[k]);
-      return bb * bb / mwx[k];
+    const T a = tile_row_sum<G, T>(d.A.rp, d.A.ci, d.A.val, tile, d.m, [&](int k, T v) {
+      const T bb = v * d.ex[k];
+      return bb * bb * T(imwx[k]);
     });
     const long long j = tile + ti.lane;
     if (j < d.m) {
-      const double dj = double(d.dy[j]);
-      const double sg = d.sig[j];
-      const double er = double(d.er[j]);
-      const double br = dj * er;
-      const double mwr = er * er * sg + br;
-      d.taur[j] = T(er * er * (0.99 / mwr));
-      d.itaur[j] = T(mwr / (0.99 * er * er));
-      double my = a * dj * dj + br * br / mwr;
+      const T dj = d.dy[j];
+      const T sg = T(d.sig[j]);
+      const T er = d.er[j];
+      const T br = dj * er;
+      const T mwr = er * er * sg + br;
+      d.taur[j] = er * er * (T(0.99) / mwr);
+      d.itaur[j] = mwr / (T(0.99) * er * er);
+      T my = a * dj * dj + br * br / mwr;
       if (j >= d.mE) {
-        const double es = double(d.es[j]);
-        const double bs = dj * es;
-        const double mws = fmax(bs, sqrt(sg * bs * bs));
-        d.taus[j] = T(es * es * (0.99 / mws));
-        d.itaus[j] = T(mws / (0.99 * es * es));
+        const T es = d.es[j];
+        const T bs = dj * es;
+        const T mws = fmax(bs, sqrt(sg * bs * bs));
+        d.taus[j] = es * es * (T(0.99) / mws);
+        d.itaus[j] = mws / (T(0.99) * es * es);
         my += bs * bs / mws;
       }
-      d.eta[j] = T(dj * dj * (0.99 / my));
-      d.ieta[j] = T(my / (0.99 * dj * dj));
+      d.eta[j] = dj * dj * (T(0.99) / my);
+      d.ieta[j] = my / (T(0.99) * dj * dj);
     }
   }
 }
@@ -862,13 +910,13 @@ __global__ void k_totals(Dev<T> d, double *out) {
   }
 }
 
-// Restart metric of the inner start (single block).
-__global__ void __launch_bounds__(kRedThreads) k_inner_begin(DevState *st, const double *part, int nb_r, int nb_c) {
+// Restart metric of the inner start (last block of the mode-1 check).
+__device__ void inner_begin_body(DevState *st, const double *part, int nb_r, int nb_c) {
   double a[16], b[16];
   final_reduce<16>(part + P_CK_R * kMaxBlocks, nb_r, CK_MAXMASK, a);
   final_reduce<16>(part + P_CK_C * kMaxBlocks, nb_c, CK_MAXMASK, b);
   if (threadIdx.x != 0) return;
-  const double om = st->omega;  // restart metric of the inner start
+  const double om = st->omega;
   st->k_restart = sqrt(om * (a[4] + b[4]) + (a[5] + b[5]) / om);
   st->k_last = INFINITY;
   st->status = ST_RUNNING;

@@ -82,27 +82,25 @@ __global__ void k_absmax(const double *v, long long n, double *part) {
   block_reduce_store<1>(q, 1u, part);
 }
 
-// Generic single-block reduction of nq quantities (q-th row of part) -> out.
-__global__ void __launch_bounds__(kRedThreads) k_reduce_rows(const double *part, int nq, int nb, unsigned max_mask,
-                                                             double *out) {
-  __shared__ double sm[kRedThreads / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int q = 0; q < nq; ++q) {
-    const bool mx = (max_mask >> q) & 1u;
-    double a = 0.0;
-    for (int b = threadIdx.x; b < nb; b += kRedThreads) {
-      const double p = part[(long long)q * kMaxBlocks + b];
-      a = mx ? fmax(a, p) : a + p;
-    }
-    a = mx ? warp_max(a) : warp_sum(a);
-    if (lane == 0) sm[wid] = a;
-    __syncthreads();
-    if (wid == 0) {
-      double c = lane < kRedThreads / 32 ? sm[lane] : 0.0;
-      c = mx ? warp_max(c) : warp_sum(c);
-      if (lane == 0) out[q] = c;
-    }
-    __syncthreads();
+// Reduction of nq quantities (row q of part, nb partials each) -> out[q]:
+// block q reduces quantity q (fixed order: lane-strided serial sums, then a
+// serial sum of the 32 lane sums).
+__global__ void __launch_bounds__(32) k_reduce_rows(const double *part, int nq, int nb, unsigned max_mask, double *out) {
+  __shared__ double ls[32];
+  const int q = blockIdx.x, lane = threadIdx.x;
+  if (q >= nq) return;
+  const bool mx = q < 32 && ((max_mask >> q) & 1u);
+  double a = 0.0;
+  for (int b = lane; b < nb; b += 32) {
+    const double p = part[(long long)q * kMaxBlocks + b];
+    a = mx ? fmax(a, p) : a + p;
+  }
+  ls[lane] = a;
+  __syncwarp();
+  if (lane == 0) {
+    double r = ls[0];
+    for (int k = 1; k < 32; ++k) r = mx ? fmax(r, ls[k]) : r + ls[k];
+    out[q] = r;
   }
 }
 

@@ -50,7 +50,8 @@ struct Params {
   double gamma_override = 0.0;
   int chunk = 128;
   long long iter_budget = 4000000000000000000LL;
-  int g_rows = 0, g_cols = 0;  // lanes per CSR row (0 = from the mean row length)
+  int g_rows = 0, g_cols = 0;  // entries per lane per CSR-stream chunk (0 = from the mean row length)
+  int cond_graph = 1;          // 1: device-driven WHILE/IF graph; 0: unrolled slots (profilable)
 };
 
 struct Result {
@@ -72,6 +73,7 @@ class SolverBase {
   virtual int debug_inner(Params &prm, int nck, const int64_t *ck, double *snap, std::string *err) = 0;
   virtual int replay(int which, int reps) = 0;
   virtual double kernel_bytes(int which) const = 0;
+  virtual double last_replay_ms() const = 0;
   virtual double gamma() const = 0;
   virtual double lambda_min() const = 0;
   virtual void set_gamma(double g) = 0;

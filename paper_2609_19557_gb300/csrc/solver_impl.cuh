@@ -49,6 +49,8 @@ class Solver : public SolverBase {
   ~Solver() override {
     if (s_) cudaStreamSynchronize(s_);
     if (gexec_) cudaGraphExecDestroy(gexec_);
+    for (cudaEvent_t e : replay_ev_)
+      if (e) cudaEventDestroy(e);
     for (void *p : allocs_) cudaFree(p);
     if (hst_) cudaFreeHost(hst_);
     if (own_stream_) cudaStreamDestroy(s_);
@@ -113,10 +115,41 @@ class Solver : public SolverBase {
     DevState run = saved;
     run.status = ST_RUNNING;
     PDNQP_CK(cudaMemcpyAsync(st_, &run, sizeof(DevState), cudaMemcpyHostToDevice, s_));
-    for (int k = 0; k < reps; ++k) {
-      if (which == 0) launch_cols();
-      else if (which == 1) launch_rows();
+    const int kind = which & 3;
+    auto one = [&]() {
+      if (kind == 0) launch_cols();
+      else if (kind == 1) launch_rows();
       else launch_primal();
+    };
+    if (which & 8) {
+      // The same launches captured as one CUDA graph (per-node cost as in the solve).
+      cudaGraph_t g;
+      PDNQP_CK(cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal));
+      for (int k = 0; k < reps; ++k) one();
+      PDNQP_CK(cudaStreamEndCapture(s_, &g));
+      cudaGraphExec_t ge;
+      cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        last_err_ = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+        return PDNQP_ERR_CUDA;
+      }
+      PDNQP_CK(cudaGraphUpload(ge, s_));
+      PDNQP_CK(cudaStreamSynchronize(s_));
+      if (replay_ev_[0] == nullptr) {
+        PDNQP_CK(cudaEventCreate(&replay_ev_[0]));
+        PDNQP_CK(cudaEventCreate(&replay_ev_[1]));
+      }
+      PDNQP_CK(cudaEventRecord(replay_ev_[0], s_));
+      PDNQP_CK(cudaGraphLaunch(ge, s_));
+      PDNQP_CK(cudaEventRecord(replay_ev_[1], s_));
+      PDNQP_CK(cudaStreamSynchronize(s_));
+      float ms = 0.f;
+      PDNQP_CK(cudaEventElapsedTime(&ms, replay_ev_[0], replay_ev_[1]));
+      last_replay_ms_ = ms;
+      cudaGraphExecDestroy(ge);
+    } else {
+      for (int k = 0; k < reps; ++k) one();
     }
     PDNQP_CK(cudaMemcpyAsync(st_, &saved, sizeof(DevState), cudaMemcpyHostToDevice, s_));
     PDNQP_CK(cudaStreamSynchronize(s_));
@@ -125,6 +158,8 @@ class Solver : public SolverBase {
 
   // Compulsory DRAM bytes (each array touched once, int32 indices, value size
   // sizeof(T)); gathers of x / y assumed L2-resident.
+  double last_replay_ms() const override { return last_replay_ms_; }
+
   double kernel_bytes(int which) const override {
     const double v = sizeof(T), n = n_, m = m_, mI = m_ - mE_;
     const double mat_h = (v + 4) * nnzH_ + 4 * (n + 1), mat_a = (v + 4) * nnzA_ + 4 * (m + 1);
@@ -177,7 +212,7 @@ class Solver : public SolverBase {
   int grid_rows_g(long long rows, int g) const { return grid_for(rows, kBlock / g); }
 
   int reduce_to_host(int nq, int nb, unsigned mask, double *out) {
-    k_reduce_rows<<<1, kRedThreads, 0, s_>>>(part_, nq, nb, mask, dred_);
+    k_reduce_rows<<<nq, 32, 0, s_>>>(part_, nq, nb, mask, dred_);
     PDNQP_CK(cudaGetLastError());
     PDNQP_CK(cudaMemcpyAsync(hred_.data(), dred_, sizeof(double) * nq, cudaMemcpyDeviceToHost, s_));
     PDNQP_CK(cudaStreamSynchronize(s_));
@@ -331,7 +366,7 @@ class Solver : public SolverBase {
       for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
         dim3 grid(nbd, j + 1);
         k_multidot<<<grid, kBlock, 0, s_>>>(V_, n, w, part_lz());
-        k_reduce_rows<<<1, kRedThreads, 0, s_>>>(part_lz(), j + 1, nbd, 0u, hdev_);
+        k_reduce_rows<<<j + 1, 32, 0, s_>>>(part_lz(), j + 1, nbd, 0u, hdev_);
         k_multiaxpy<<<grid_n(), kBlock, 0, s_>>>(V_, n, hdev_, j + 1, w);
       }
       double b2;
@@ -444,6 +479,10 @@ class Solver : public SolverBase {
     d.sig = sig_;
     d.part = part_;
     d.st = st_;
+    PDNQP_TRY(dalloc(&d.ctr, 4));
+    PDNQP_CK(cudaMemsetAsync(d.ctr, 0, 4 * sizeof(unsigned), s_));
+    d.hw = 0;
+    d.hc = 0;
     PDNQP_CK(cudaGetLastError());
     return 0;
   }
@@ -457,27 +496,38 @@ class Solver : public SolverBase {
     with_G(gA_, [&](auto GG) { k_rows<T, decltype(GG)::value><<<nb_rows(), kBlock, 0, s_>>>(d_); });
   }
   void launch_cols() {
-    with_G(gN_, [&](auto GG) { k_cols<T, decltype(GG)::value><<<nb_cols(), kBlock, 0, s_>>>(d_); });
+    with_G(gN_, [&](auto GG) {
+      if (d_.hw)
+        k_cols<T, decltype(GG)::value, true><<<nb_cols(), kBlock, 0, s_>>>(d_, nb_rows());
+      else
+        k_cols<T, decltype(GG)::value, false><<<nb_cols(), kBlock, 0, s_>>>(d_, nb_rows());
+    });
   }
-  static constexpr int kSlotKernels = 8;
-  void launch_trial(cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hc) {
+  // Trial: primal, rows, cols (+ decision in its last block).  Check: rows,
+  // cols (+ check decisions in its last block), apply.  The conditional
+  // handles travel in the kernels' Dev argument (captured per graph).
+  static constexpr int kSlotKernels = 6;
+  void launch_trial() {
     launch_primal();
     launch_rows();
     launch_cols();
-    k_decide<<<1, kRedThreads, 0, s_>>>(st_, part_, nb_rows(), nb_cols(), hw, hc);
   }
-  void launch_check_group(cudaGraphConditionalHandle hw) {
+  void launch_check_group() {
     launch_check(0);
-    k_check_final<<<1, kRedThreads, 0, s_>>>(st_, part_, nb_rows(), nb_cols(), hw);
     k_check_apply<T><<<grid_nm(), kBlock, 0, s_>>>(d_);
   }
   void launch_slot() {
-    launch_trial(0, 0);
-    launch_check_group(0);
+    launch_trial();
+    launch_check_group();
   }
   void launch_check(int mode) {
     with_G(gA_, [&](auto GG) { k_check_rows<T, decltype(GG)::value><<<nb_rows(), kBlock, 0, s_>>>(d_, mode); });
-    with_G(gN_, [&](auto GG) { k_check_cols<T, decltype(GG)::value><<<nb_cols(), kBlock, 0, s_>>>(d_, mode); });
+    with_G(gN_, [&](auto GG) {
+      if (d_.hw)
+        k_check_cols<T, decltype(GG)::value, true><<<nb_cols(), kBlock, 0, s_>>>(d_, mode, nb_rows());
+      else
+        k_check_cols<T, decltype(GG)::value, false><<<nb_cols(), kBlock, 0, s_>>>(d_, mode, nb_rows());
+    });
   }
 
   // Lanes per CSR row: parameter override, else the mean-row-length choice of setup.
@@ -486,8 +536,10 @@ class Solver : public SolverBase {
     gN_ = prm.g_cols > 0 ? prm.g_cols : gN0_;
   }
 
-  int build_graph(int chunk) {
-    if (gexec_ && chunk == graph_chunk_ && gA_ == graph_gA_ && gN_ == graph_gN_) return 0;
+  int build_graph(int chunk, int cond) {
+    if (gexec_ && chunk == graph_chunk_ && gA_ == graph_gA_ && gN_ == graph_gN_ && cond == graph_cond_) return 0;
+    graph_cond_ = cond;
+    use_cond_ = cond != 0;
     graph_gA_ = gA_;
     graph_gN_ = gN_;
     if (gexec_) {
@@ -520,6 +572,8 @@ class Solver : public SolverBase {
     cudaGraph_t g = nullptr;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return -1;
     auto fail = [&]() {
+      d_.hw = 0;
+      d_.hc = 0;
       cudaStreamCaptureStatus cs;
       if (cudaStreamIsCapturing(s_, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
         cudaGraph_t junk;
@@ -550,7 +604,9 @@ class Solver : public SolverBase {
     cudaGraph_t body = wp.conditional.phGraph_out[0];
     if (cudaStreamBeginCaptureToGraph(s_, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return fail();
-    launch_trial(hw, hc);
+    d_.hw = hw;
+    d_.hc = hc;
+    launch_trial();
     cudaStreamCaptureStatus cst;
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
@@ -569,7 +625,9 @@ class Solver : public SolverBase {
     cudaGraph_t cbody = ip.conditional.phGraph_out[0];
     if (cudaStreamBeginCaptureToGraph(s_, cbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return fail();
-    launch_check_group(hw);
+    launch_check_group();
+    d_.hw = 0;
+    d_.hc = 0;
     cudaGraph_t cbody_out = nullptr;
     if (cudaStreamEndCapture(s_, &cbody_out) != cudaSuccess) return fail();
     if (cudaGraphInstantiate(&gexec_, g, 0) != cudaSuccess) return fail();
@@ -676,8 +734,7 @@ class Solver : public SolverBase {
     S.beta_nec = prm.beta_nec;
     S.beta_art = prm.beta_art;
     PDNQP_CK(cudaMemcpyAsync(st_, &S, sizeof(S), cudaMemcpyHostToDevice, s_));
-    launch_check(1);
-    k_inner_begin<<<1, kRedThreads, 0, s_>>>(st_, part_, nb_rows(), nb_cols());
+    launch_check(1);  // its last block sets the restart metric of the start and the running status
     launches_ += 9 + 3LL * prm.ruiz_inner;
     PDNQP_CK(cudaGetLastError());
     return 0;
@@ -692,16 +749,16 @@ class Solver : public SolverBase {
 
   // Runs graph chunks until the device status leaves RUNNING.
   int run_until_stop(const Params &prm, DevState *S, double t0) {
-    PDNQP_TRY(build_graph(prm.chunk));
+    PDNQP_TRY(build_graph(prm.chunk, prm.cond_graph));
     long long tr0 = -1, ac0 = 0;
     for (;;) {
       PDNQP_CK(cudaGraphLaunch(gexec_, s_));
       PDNQP_TRY(read_state(S));
       if (use_cond_) {
-        // 4 kernels per trial, 4 more per check, 1 loop-begin kernel per launch.
+        // 3 kernels per trial, 3 more per check, 1 loop-begin kernel per launch.
         if (tr0 < 0) tr0 = trials_, ac0 = accepted_;
         launches_ += 1;
-        launches_ += 4 * (S->trials - tr0) + 4 * ((S->accepted_all / std::max<long long>(1, prm.k_chk)) -
+        launches_ += 3 * (S->trials - tr0) + 3 * ((S->accepted_all / std::max<long long>(1, prm.k_chk)) -
                                                   (ac0 / std::max<long long>(1, prm.k_chk)));
         tr0 = S->trials;
         ac0 = S->accepted_all;
@@ -744,14 +801,14 @@ class Solver : public SolverBase {
         k_outer_rows<T, decltype(GG)::value><<<nbr, kBlock, 0, s_>>>(d_, Ad_, lcd_, ucd_, Dc_, lam_, sig_, rcur_,
                                                                       update);
       });
-      k_reduce_rows<<<1, kRedThreads, 0, s_>>>(part_, 12, nbr, OUT_MAXMASK, dred_);
+      k_reduce_rows<<<12, 32, 0, s_>>>(part_, 12, nbr, OUT_MAXMASK, dred_);
     }
     // A' lambda uses the updated multipliers: launched after the row kernel.
     with_G(gN_, [&](auto GG) {
       k_outer_cols<T, decltype(GG)::value><<<nbc, kBlock, 0, s_>>>(d_, Hd_, Atd_, c_, lxd_, uxd_, Dx_, lam_, z_,
                                                                     ginv, cs_);
     });
-    k_reduce_rows<<<1, kRedThreads, 0, s_>>>(part_ + 12 * kMaxBlocks, 12, nbc, OUT_MAXMASK, dred_ + 12);
+    k_reduce_rows<<<12, 32, 0, s_>>>(part_ + 12 * kMaxBlocks, 12, nbc, OUT_MAXMASK, dred_ + 12);
     PDNQP_CK(cudaGetLastError());
     PDNQP_CK(cudaMemcpyAsync(hred_.data(), dred_, sizeof(double) * 24, cudaMemcpyDeviceToHost, s_));
     PDNQP_CK(cudaStreamSynchronize(s_));
@@ -948,8 +1005,11 @@ class Solver : public SolverBase {
   DevState *st_ = nullptr, *hst_ = nullptr;
   Dev<T> d_{};
   cudaGraphExec_t gexec_ = nullptr;
+  cudaEvent_t replay_ev_[2] = {nullptr, nullptr};
+  float last_replay_ms_ = 0.f;
   int graph_chunk_ = 0;
   bool use_cond_ = true;  // device-driven WHILE/IF graph (else unrolled slots)
+  int graph_cond_ = -1;
   double cs_ = 1.0, qnorm_ = 0.0, gamma_ = 1.0, lam_min_ = 0.0, sigma0_ = 1.0, omega_ = 1.0;
   double gamma_pending_ = 0.0;
   long long trials_ = 0, accepted_ = 0, restarts_ = 0, launches_ = 0;

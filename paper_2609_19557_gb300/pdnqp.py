@@ -25,7 +25,7 @@ SNAP_SCALARS = 8
 EXPORTED = ["pdnqp_create", "pdnqp_create_ex", "pdnqp_destroy", "pdnqp_solve", "pdnqp_get", "pdnqp_set_start",
             "pdnqp_set_param", "pdnqp_get_param", "pdnqp_dims", "pdnqp_last_error", "pdnqp_debug_inner",
             "pdnqp_replay_kernel", "pdnqp_kernel_bytes", "pdnqp_kkt_residuals", "pdnqp_kkt_last_error",
-            "pdnqp_kkt_residuals_noalloc"]
+            "pdnqp_kkt_residuals_noalloc", "pdnqp_replay_last_ms"]
 
 
 class pdnqp_csr(C.Structure):
@@ -88,6 +88,8 @@ def load(path: str | None = None):
     L.pdnqp_last_error.restype = C.c_char_p
     L.pdnqp_debug_inner.argtypes = [vp, ip, vp, vp]
     L.pdnqp_replay_kernel.argtypes = [vp, ip, ip]
+    L.pdnqp_replay_last_ms.argtypes = [vp]
+    L.pdnqp_replay_last_ms.restype = C.c_double
     L.pdnqp_kernel_bytes.argtypes = [vp, ip, C.POINTER(C.c_double)]
     L.pdnqp_kkt_residuals.argtypes = [C.POINTER(pdnqp_device_problem), vp, vp, vp, vp]
     L.pdnqp_kkt_residuals_noalloc.argtypes = [C.POINTER(pdnqp_device_problem), vp, vp, vp, vp]
@@ -220,6 +222,10 @@ def pdnqp_debug_inner(h: Handle, checkpoints):
 
 def pdnqp_replay_kernel(h: Handle, which: int, reps: int):
     _check(h.ptr, load().pdnqp_replay_kernel(h.ptr, int(which), int(reps)))
+
+
+def pdnqp_replay_last_ms(h: Handle) -> float:
+    return load().pdnqp_replay_last_ms(h.ptr)
 
 
 def pdnqp_kernel_bytes(h: Handle, which: int) -> float:
