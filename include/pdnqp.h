@@ -96,6 +96,12 @@ typedef struct {
   int64_t kernel_launches;   /* CUDA kernels launched by the last pdnqp_solve (graph nodes included) */
   double inner_seconds;      /* wall time spent in the device-driven inner loops (Algorithm 4 iterations) */
   double setup_seconds;      /* wall time of the per-outer-iteration inner setup (warm start, scaling, steps) */
+  double loop_seconds;       /* device time (CUDA events) of the persistent trial-loop launches; 0 in graph modes */
+  int64_t loop_trials;       /* trials run inside those launches */
+  int64_t loop_blocks;       /* blocks of the persistent launch (0: graph modes) */
+  double loop_phase_seconds[6]; /* device time of their passes as seen by block 0 (globaltimer): primal work,
+                                   primal barrier wait, row work, row barrier wait, column work, column barrier
+                                   wait + acceptance decision */
 } pdnqp_residuals;
 
 /* Creation options (pdnqp_create uses precision = PDNQP_FP64, device = current,
@@ -151,9 +157,14 @@ PDNQP_API int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0);
  * iter_budget (cap on accepted inner iterations per pdnqp_solve, summed over
  * outer iterations; ITER_LIMIT when reached), g_rows / g_cols (nonzeros per
  * lane per CSR-stream chunk in the row / column SpMV kernels: 4, 8 or 16; 0 =
- * from the mean row length), cond_graph (1: inner loop as a device-driven
- * CUDA graph with conditional WHILE/IF nodes; 0: unrolled graph of `chunk`
- * trial slots, which profilers can inspect kernel by kernel).
+ * from the mean row length), persistent (1, the default: the trials of the
+ * inner loop run inside one cooperative kernel launch per check period, with
+ * bounded grid barriers between the primal, row and column passes; used when
+ * the device supports cooperative launches, else the graph modes below),
+ * loop_blocks_per_sm (blocks per SM of that launch; 0 = as many as fit),
+ * cond_graph (with persistent = 0; 1: inner loop as a device-driven CUDA
+ * graph with conditional WHILE/IF nodes; 0: unrolled graph of `chunk` trial
+ * slots, which profilers can inspect kernel by kernel).
  * Returns PDNQP_ERR_ARG for an unknown name or an out-of-range value. */
 PDNQP_API int pdnqp_set_param(pdnqp_t *h, const char *name, double value);
 PDNQP_API int pdnqp_get_param(const pdnqp_t *h, const char *name, double *value);

@@ -334,6 +334,10 @@ int pdnqp_get(const pdnqp_t *h, double *x, double *y, pdnqp_residuals *r) {
     r->kernel_launches = R.launches;
     r->inner_seconds = R.inner_seconds;
     r->setup_seconds = R.setup_seconds;
+    r->loop_seconds = R.loop_seconds;
+    r->loop_trials = R.loop_trials;
+    r->loop_blocks = R.loop_blocks;
+    for (int k = 0; k < 6; ++k) r->loop_phase_seconds[k] = R.loop_phase_seconds[k];
   }
   return 0;
 }
@@ -361,7 +365,8 @@ int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0) {
   X(beta_suff, d, 0.0, 1.0) X(beta_nec, d, 0.0, 1.0) X(beta_art, d, 0.0, 1.0)                      \
   X(rej_limit, i, 1.0, 1e9) X(kappa_shrink, d, 1e-6, 0.999999) X(delta_sigma, d, 1.0, 1e300)       \
   X(sigma_max, d, 1e-300, 1e300) X(tol_floor, d, 0.0, 1.0) X(chunk, i, 1.0, 65536.0)               \
-  X(g_rows, i, 0.0, 16.0) X(g_cols, i, 0.0, 16.0) X(iter_budget, ll, 1.0, 4e18) X(cond_graph, i, 0.0, 1.0)
+  X(g_rows, i, 0.0, 16.0) X(g_cols, i, 0.0, 16.0) X(iter_budget, ll, 1.0, 4e18) X(cond_graph, i, 0.0, 1.0) \
+  X(persistent, i, 0.0, 1.0) X(loop_blocks_per_sm, i, 0.0, 32.0)
 
 int pdnqp_set_param(pdnqp_t *h, const char *name, double value) {
   if (!h || !name) return fail(h, PDNQP_ERR_ARG, "NULL handle or name");

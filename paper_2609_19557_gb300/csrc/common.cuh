@@ -125,30 +125,167 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NQ], const unsign
   }
 }
 
+// Grid barrier of a cooperative (co-resident) launch.  bar[0] counts the
+// arrivals, bar[kBarGen] is the generation, bar[kBarFault] the fault flag.  The last block to
+// arrive runs lead() with all its threads before it releases the others, so
+// lead() sees every block's writes from before the barrier and every block
+// sees lead()'s writes after it.  The wait is bounded: a block that polls
+// kSpinLimit times without a release (about a second or more), or that sees
+// the fault flag, sets the flag and the call returns false; the caller then
+// leaves the kernel, so a barrier that can never complete ends the launch
+// instead of hanging it.
+constexpr unsigned kSpinLimit = 1u << 22;
+constexpr unsigned kSpinLimitTx = 1u << 24;  // polls of a bulk-copy barrier (with a 32 ns sleep)
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory mbarriers and bulk (TMA) copies global -> shared.  One thread
+// arms a barrier with the byte count it expects and issues the copies; the
+// barrier's phase completes when the bytes have landed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// Makes barrier initialisation visible to the copy engine (async proxy).
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Orders this thread's earlier shared-memory accesses before later bulk copies.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// Bulk copy of `bytes` (multiple of 16; both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// Bounded wait for the phase with the given parity, by thread 0 for its block:
+// the result is block-uniform (every thread returns it).  On success every
+// thread also observes the completed phase itself (immediately), which makes
+// the copied bytes visible to it.  On a timeout the fault flag is set and the
+// copies in flight get a second bounded wait before the block gives up, so no
+// copy is left writing into shared memory of a block that has left.
+__device__ __forceinline__ bool mbar_wait_block(unsigned long long *bar, unsigned parity, unsigned *fault) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    int r = 0;
+    for (unsigned it = 0; it <= kSpinLimitTx; ++it) {
+      if (mbar_test(bar, parity)) {
+        r = 1;
+        break;
+      }
+      __nanosleep(32);
+    }
+    if (!r) {
+      atomicExch(fault, 1u);
+      for (unsigned it = 0; it <= kSpinLimitTx; ++it) {
+        if (mbar_test(bar, parity)) break;
+        __nanosleep(32);
+      }
+    }
+    ok = r;
+  }
+  __syncthreads();
+  const bool r = ok != 0;
+  if (r)
+    for (unsigned it = 0; it <= kSpinLimitTx && !mbar_test(bar, parity); ++it) {
+    }
+  return r;
+}
+
+// Device-wide nanosecond timer (phase timing of the persistent loop).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Word offsets of the barrier's generation and fault flag from its arrival
+// counter: each on its own 128-byte line, so that the polls of the
+// generation do not queue behind the arrival atomics.
+constexpr int kBarGen = 32, kBarFault = 64, kBarWords = 96;
+
+template <typename F>
+__device__ __forceinline__ bool grid_sync(unsigned *bar, F lead) {
+  __shared__ int role;  // 0 released, 1 leader, 2 fault
+  unsigned gen = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    gen = ld_acquire_gpu(bar + kBarGen);
+    __threadfence();
+    role = (atomicAdd(bar, 1u) == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (role == 1) {
+    __threadfence();
+    lead();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      st_release_gpu(bar + kBarGen, gen + 1);
+    }
+  } else if (threadIdx.x == 0) {
+    unsigned it = 0;
+    while (ld_acquire_gpu(bar + kBarGen) == gen) {
+      if (ld_acquire_gpu(bar + kBarFault) != 0u || ++it > kSpinLimit) {
+        atomicExch(bar + kBarFault, 1u);
+        role = 2;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return role != 2;
+}
+__device__ __forceinline__ bool grid_sync(unsigned *bar) {
+  return grid_sync(bar, [] {});
+}
+
 // Single-block final reduction of NQ quantities over nb partials (fixed order):
 // warp w handles quantities w, w + nwarps, ...; lane l sums partials l, l + 32,
-// ... serially, then lane 0 combines the 32 lane sums in order.  Every thread
+// ... serially, then a fixed butterfly combines the 32 lane sums.  Every thread
 // of the block gets out[].  blockDim.x must be a multiple of 32.
 template <int NQ>
 __device__ __forceinline__ void final_reduce(const double *part, int nb, const unsigned kind_mask, double (&out)[NQ]) {
-  __shared__ double lane_sum[NQ][32];
   __shared__ double res[NQ];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int q = wid; q < NQ; q += nw) {
     const bool mx = (kind_mask >> q) & 1u;
     double a = 0.0;
     for (int b = lane; b < nb; b += 32) {
-      const double p = part[q * kMaxBlocks + b];
+      const double p = __ldcg(part + q * kMaxBlocks + b);
       a = mx ? fmax(a, p) : a + p;
     }
-    lane_sum[q][lane] = a;
-    __syncwarp();
-    if (lane == 0) {
-      double r = lane_sum[q][0];
-      for (int k = 1; k < 32; ++k) r = mx ? fmax(r, lane_sum[q][k]) : r + lane_sum[q][k];
-      res[q] = r;
-    }
-    __syncwarp();
+    a = mx ? warp_max(a) : warp_sum(a);  // fixed butterfly: deterministic
+    if (lane == 0) res[q] = a;
   }
   __syncthreads();
 #pragma unroll
@@ -265,6 +402,67 @@ __device__ __forceinline__ Acc tile_stream(const int *__restrict__ rp, const int
     __syncwarp();
   }
   return acc;
+}
+
+// Two CSR matrices with the same rows streamed together over one warp tile
+// (the column pass: Q and A^T): both row-pointer pairs, then in every trip
+// one chunk of each matrix, so the two dependent load chains (row pointers ->
+// entries -> gathers) overlap instead of running one after the other.  Lane l
+// gets the sums of row tile + l of both matrices in o1, o2.
+template <int K1, int K2, typename Acc, typename T, typename F1, typename F2>
+__device__ __forceinline__ void tile_pair_sum(const int *__restrict__ rp1, const int *__restrict__ ci1,
+                                              const T *__restrict__ v1, const int *__restrict__ rp2,
+                                              const int *__restrict__ ci2, const T *__restrict__ v2, long long tile,
+                                              long long nrows, F1 f1, F2 f2, Acc &o1, Acc &o2) {
+  const int lane = threadIdx.x & 31;
+  Acc *sb1 = warp_stage_buffer<K1, Acc>();
+  __shared__ Acc buf2[kBlock / 32][32 * K2];
+  Acc *sb2 = buf2[threadIdx.x >> 5];
+  const long long my = tile + lane;
+  const long long last = (nrows - 1 - tile) < 31 ? (nrows - 1 - tile) : 31;
+  int rb1 = 0, re1 = 0, rb2 = 0, re2 = 0;
+  if (my < nrows) {
+    rb1 = rp1[my];
+    re1 = rp1[my + 1];
+    rb2 = rp2[my];
+    re2 = rp2[my + 1];
+  }
+  const int base1 = __shfl_sync(0xffffffffu, rb1, 0), end1 = __shfl_sync(0xffffffffu, re1, (int)last);
+  const int base2 = __shfl_sync(0xffffffffu, rb2, 0), end2 = __shfl_sync(0xffffffffu, re2, (int)last);
+  if (my >= nrows) {
+    rb1 = re1 = end1;
+    rb2 = re2 = end2;
+  }
+  Acc a1 = Acc(0), a2 = Acc(0);
+  for (int c1 = base1, c2 = base2; c1 < end1 || c2 < end2; c1 += 32 * K1, c2 += 32 * K2) {
+    Acc p1[K1], p2[K2];
+#pragma unroll
+    for (int j = 0; j < K1; ++j) {
+      const int k = c1 + j * 32 + lane;
+      p1[j] = k < end1 ? f1(ci1[k], v1[k]) : Acc(0);
+    }
+#pragma unroll
+    for (int j = 0; j < K2; ++j) {
+      const int k = c2 + j * 32 + lane;
+      p2[j] = k < end2 ? f2(ci2[k], v2[k]) : Acc(0);
+    }
+#pragma unroll
+    for (int j = 0; j < K1; ++j) sb1[j * 32 + lane] = p1[j];
+#pragma unroll
+    for (int j = 0; j < K2; ++j) sb2[j * 32 + lane] = p2[j];
+    __syncwarp();
+    {
+      const int lo = rb1 > c1 ? rb1 : c1, hi = re1 < c1 + 32 * K1 ? re1 : c1 + 32 * K1;
+      for (int k = lo; k < hi; ++k) a1 += sb1[k - c1];
+    }
+    {
+      const int lo = rb2 > c2 ? rb2 : c2, hi = re2 < c2 + 32 * K2 ? re2 : c2 + 32 * K2;
+      for (int k = lo; k < hi; ++k) a2 += sb2[k - c2];
+    }
+    __syncwarp();
+  }
+  o1 = a1;
+  o2 = a2;
 }
 
 template <int K, typename Acc, typename T, typename F>

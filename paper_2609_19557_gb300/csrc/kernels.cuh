@@ -36,6 +36,9 @@ constexpr int P_TR_C = 4;    // trial, column kernel (same 4)
 constexpr int P_CK_R = 8;    // check, row kernel: 16 quantities
 constexpr int P_CK_C = 24;   // check, column kernel: 16 quantities
 constexpr unsigned CK_MAXMASK = 0x0F0Fu;  // quantities 0-3 and 8-11 of a check are maxima
+// Counter words (d.ctr): [0] column last-block counter, [1] check last-block
+// counter, [kCtrBar, kCtrBar + kBarWords) the grid barrier of the persistent loop.
+constexpr int kCtrBar = 128, kCtrWords = kCtrBar + kBarWords;
 
 template <typename T>
 struct Mat {
@@ -71,6 +74,7 @@ struct Dev {
   double *part;
   DevState *st;
   unsigned *ctr;   // arrival counters of the last-block reductions (reset by the last block)
+  unsigned long long *ptime;  // persistent loop: ns spent in the primal, row and column(+decision) passes
   cudaGraphConditionalHandle hw, hc;  // device-loop handles (0 when the graph has none)
 };
 
@@ -98,7 +102,7 @@ struct SumT {
 // (one coalesced load and store) instead of chains of dependent global
 // read-modify-writes.
 __device__ __forceinline__ void state_load(DevState &S, const DevState *g) {
-  for (int i = threadIdx.x; i < (int)(sizeof(DevState) / 4); i += blockDim.x) ((int *)&S)[i] = ((const int *)g)[i];
+  for (int i = threadIdx.x; i < (int)(sizeof(DevState) / 4); i += blockDim.x) ((int *)&S)[i] = __ldcg((const int *)g + i);
   __syncthreads();
 }
 __device__ __forceinline__ void state_store(DevState *g, const DevState &S) {
@@ -148,26 +152,88 @@ __device__ void inner_begin_body(DevState *st, const double *part, int nb_r, int
 
 // Primal x-block of the trial: x_tr = P_[l,u](x - tau (q + (1-alpha) H xbar +
 // alpha H x - A'y)) with the cached products H x, H xbar, A'y.
+// The phase functions below read the scalar state through `st` (global
+// memory in the one-kernel-per-phase launches, a shared-memory copy in the
+// persistent loop) and touch the iterate buffers through plain pointers: in
+// the persistent loop the same buffers are written and read across grid
+// barriers within one launch, so they must not go through the read-only path.
+// 16-byte vectors of the streaming passes (every vector is its own
+// allocation, so 256-byte aligned): W elements per load or store.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_primal(Dev<T> d) {
-  const DevState *st = d.st;
-  if (st->status != ST_RUNNING) return;
+struct Vec16;
+template <>
+struct Vec16<float> {
+  typedef float4 type;
+};
+template <>
+struct Vec16<double> {
+  typedef double2 type;
+};
+template <typename T>
+struct Pack {
+  static constexpr int W = 16 / sizeof(T);
+  T v[W];
+  __device__ __forceinline__ void load(const T *p, long long i) {
+    *reinterpret_cast<typename Vec16<T>::type *>(v) = reinterpret_cast<const typename Vec16<T>::type *>(p)[i];
+  }
+  __device__ __forceinline__ void store(T *p, long long i) const {
+    reinterpret_cast<typename Vec16<T>::type *>(p)[i] = *reinterpret_cast<const typename Vec16<T>::type *>(v);
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ void primal_phase(const Dev<T> &d, const DevState *st) {
   const int cur = st->cur, a0 = st->acur, acc = st->accepted;
   const double t = (double)st->t;
   const T alpha = T(2.0 / (t + 2.0));
   const T oma = T(1) - alpha;
   const T sc = T(st->kappa / st->omega);
   const T ap = T(st->alpha_acc), omap = T(1) - ap;
-  const T *__restrict__ x = d.x[cur];
-  const T *__restrict__ Hx = d.Hx[cur];
-  const T *__restrict__ Aty = d.Aty[cur];
-  T *__restrict__ xt = d.x[1 - cur];
-  PDNQP_GRID_STRIDE(i, d.n) {
-    const T xi = x[i], hxi = Hx[i];
-    T hxb;
+  const T *x = d.x[cur];
+  const T *Hx = d.Hx[cur];
+  const T *Aty = d.Aty[cur];
+  T *xt = d.x[1 - cur];
+  constexpr int W = Pack<T>::W;
+  const long long nv = d.n / W;
+  // W elements per thread and trip with 16-byte loads and stores; the same
+  // arithmetic per element as the scalar tail below.
+  PDNQP_GRID_STRIDE(c, nv) {
+    Pack<T> X, HX, HB, Q, AT, TA, L, U, XT;
+    X.load(x, c);
+    HX.load(Hx, c);
+    HB.load(d.Hxbar[a0], c);
+    Q.load(d.qx, c);
+    AT.load(Aty, c);
+    TA.load(d.taux, c);
+    L.load(d.lx, c);
+    U.load(d.ux, c);
     if (acc) {
       // Running averages of the previous acceptance (Algorithm 4), written to
       // the other buffer: wbar <- (1 - alpha) wbar + alpha w.
+      Pack<T> XB;
+      XB.load(d.xbar[a0], c);
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        HB.v[k] = omap * HB.v[k] + ap * HX.v[k];
+        XB.v[k] = omap * XB.v[k] + ap * X.v[k];
+      }
+      HB.store(d.Hxbar[a0 ^ 1], c);
+      XB.store(d.xbar[a0 ^ 1], c);
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      const T g = Q.v[k] + oma * HB.v[k] + alpha * HX.v[k] - AT.v[k];
+      XT.v[k] = clampv<T>(X.v[k] - (sc * TA.v[k]) * g, L.v[k], U.v[k]);
+    }
+    XT.store(xt, c);
+  }
+  // Tail (n mod W elements).
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long i = nv * W + tid;
+  if (i < d.n) {
+    const T xi = x[i], hxi = Hx[i];
+    T hxb;
+    if (acc) {
       hxb = omap * d.Hxbar[a0][i] + ap * hxi;
       d.Hxbar[a0 ^ 1][i] = hxb;
       d.xbar[a0 ^ 1][i] = omap * d.xbar[a0][i] + ap * xi;
@@ -179,6 +245,12 @@ __global__ void __launch_bounds__(kBlock) k_primal(Dev<T> d) {
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_primal(Dev<T> d) {
+  if (d.st->status != ST_RUNNING) return;
+  primal_phase<T>(d, d.st);
+}
+
 // Constraint rows: (A x_tr)_j, the s/r blocks of the primal trial, B w_tr,
 // the dual trial y_tr = y + eta (h - B w_tr - beta (B w_tr - B w)), and the
 // row-local terms of the acceptance sums.  Steps are used as
@@ -186,46 +258,54 @@ __global__ void __launch_bounds__(kBlock) k_primal(Dev<T> d) {
 // dw^2 / tau and dy^2 / eta are accumulated with the stored inverses 1/tau0,
 // 1/eta0 and scaled once by omega / kappa and 1 / (kappa omega).
 template <typename T, int G>
-__global__ void __launch_bounds__(kBlock) k_rows(Dev<T> d) {
-  const DevState *st = d.st;
-  if (st->status != ST_RUNNING) return;
+__device__ __forceinline__ void rows_phase(const Dev<T> &d, const DevState *st) {
   const int cur = st->cur, nx = 1 - cur, a0 = st->acur, acc = st->accepted;
   const double t = (double)st->t;
   const T alpha = T(2.0 / (t + 2.0)), oma = T(1) - alpha;
   const T beta = T(t / (t + 1.0));
   const T sct = T(st->kappa / st->omega), sce = T(st->kappa * st->omega);
   const T ap = T(st->alpha_acc), omap = T(1) - ap;
-  const T *__restrict__ xt = d.x[nx];
+  const T *xt = d.x[nx];
   T Lt = T(0), Le = T(0), RH = T(0), RB = T(0);
   TileIter ti;
   for (long long tile = ti.first; tile < d.m; tile += ti.step) {
-    const T ax = tile_row_sum<G, T>(d.A.rp, d.A.ci, d.A.val, tile, d.m, [&](int k, T a) { return a * xt[k]; });
     const long long j = tile + ti.lane;
-    if (j < d.m) {
-      const T y = d.y[cur][j], r = d.r[cur][j];
+    const bool valid = j < d.m, ineq = j >= d.mE;
+    // Everything that does not need (A x_tr)_j first (the r and s blocks of
+    // the trial and the operands of the dual step), so that these loads
+    // overlap the SpMV chain.
+    T y = T(0), r = T(0), rt = T(0), stv = T(0), ds = T(0), bw = T(0), etj = T(0), hpj = T(0), sig = T(0);
+    if (valid) {
+      y = d.y[cur][j];
+      r = d.r[cur][j];
       T rb;
       if (acc) {  // running averages of the previous acceptance
         rb = omap * d.rbar[a0][j] + ap * r;
         d.rbar[a0 ^ 1][j] = rb;
         d.ybar[a0 ^ 1][j] = omap * d.ybar[a0][j] + ap * y;
-        if (j >= d.mE) d.sbar[a0 ^ 1][j] = omap * d.sbar[a0][j] + ap * d.s[cur][j];
+        if (ineq) d.sbar[a0 ^ 1][j] = omap * d.sbar[a0][j] + ap * d.s[cur][j];
       } else {
         rb = d.rbar[a0][j];
       }
-      const T sig = T(d.sig[j]);
-      const T rt = r - (sct * d.taur[j]) * (d.qr[j] + sig * (oma * rb + alpha * r) + y);
-      T bwt = ax - rt, ds = T(0);
-      if (j >= d.mE) {
+      sig = T(d.sig[j]);
+      rt = r - (sct * d.taur[j]) * (d.qr[j] + sig * (oma * rb + alpha * r) + y);
+      d.r[nx][j] = rt;
+      if (ineq) {
         const T s = d.s[cur][j];
-        const T stv = clampv<T>(s - (sct * d.taus[j]) * (d.qs[j] + y), d.ls[j], d.us[j]);
+        stv = clampv<T>(s - (sct * d.taus[j]) * (d.qs[j] + y), d.ls[j], d.us[j]);
         d.s[nx][j] = stv;
-        bwt -= stv;
         ds = stv - s;
         Lt += ds * ds * d.itaus[j];
       }
-      const T bw = d.Bw[cur][j];
-      const T yt = y + (sce * d.eta[j]) * (d.hp[j] - bwt - beta * (bwt - bw));
-      d.r[nx][j] = rt;
+      bw = d.Bw[cur][j];
+      etj = d.eta[j];
+      hpj = d.hp[j];
+    }
+    const T ax = tile_row_sum<G, T>(d.A.rp, d.A.ci, d.A.val, tile, d.m, [&](int k, T a) { return a * __ldcg(xt + k); });
+    if (valid) {
+      T bwt = ax - rt;
+      if (ineq) bwt -= stv;
+      const T yt = y + (sce * etj) * (hpj - bwt - beta * (bwt - bw));
       d.Bw[nx][j] = bwt;
       d.y[nx][j] = yt;
       const T dr = rt - r, dyv = yt - y;
@@ -239,41 +319,435 @@ __global__ void __launch_bounds__(kBlock) k_rows(Dev<T> d) {
   block_reduce_store<4>(v, 0u, d.part + P_TR_R * kMaxBlocks);
 }
 
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_rows(Dev<T> d) {
+  if (d.st->status != ST_RUNNING) return;
+  rows_phase<T, G>(d, d.st);
+}
+
 // Variable rows: (H x_tr)_i and (A' y_tr)_i (the products with Q and A^T),
 // plus the x terms of the acceptance sums.
-template <typename T, int G, bool COND>
-__global__ void __launch_bounds__(kBlock) k_cols(Dev<T> d, int nb_r) {
-  const DevState *st = d.st;
-  if (st->status != ST_RUNNING) {
-    stop_loop<COND>(d.hw, d.hc);
-    return;
-  }
+template <typename T, int GH, int GT>
+__device__ __forceinline__ void cols_phase(const Dev<T> &d, const DevState *st) {
   const int cur = st->cur, nx = 1 - cur;
-  const T *__restrict__ xt = d.x[nx];
-  const T *__restrict__ yt = d.y[nx];
+  const T *xt = d.x[nx];
+  const T *yt = d.y[nx];
   T Lt = T(0), RH = T(0), RB = T(0);
   TileIter ti;
   for (long long tile = ti.first; tile < d.n; tile += ti.step) {
-    const T hx = tile_row_sum<G, T>(d.H.rp, d.H.ci, d.H.val, tile, d.n, [&](int k, T a) { return a * xt[k]; });
-    const T aty = tile_row_sum<G, T>(d.At.rp, d.At.ci, d.At.val, tile, d.n, [&](int k, T a) { return a * yt[k]; });
     const long long i = tile + ti.lane;
+    // Row-local operands first: their loads overlap the SpMV chains.
+    T xti = T(0), xci = T(0), hxc = T(0), atc = T(0), itx = T(0);
+    if (i < d.n) {
+      xti = xt[i];
+      xci = d.x[cur][i];
+      hxc = d.Hx[cur][i];
+      atc = d.Aty[cur][i];
+      itx = d.itaux[i];
+    }
+    T hx, aty;
+    tile_pair_sum<GH, GT, T>(
+        d.H.rp, d.H.ci, d.H.val, d.At.rp, d.At.ci, d.At.val, tile, d.n,
+        [&](int k, T a) { return a * __ldcg(xt + k); }, [&](int k, T a) { return a * __ldcg(yt + k); }, hx, aty);
     if (i < d.n) {
       d.Hx[nx][i] = hx;
       d.Aty[nx][i] = aty;
-      const T dx = xt[i] - d.x[cur][i];
-      const T dh = hx - d.Hx[cur][i];
-      const T da = aty - d.Aty[cur][i];
-      Lt += dx * dx * d.itaux[i];
+      const T dx = xti - xci;
+      const T dh = hx - hxc;
+      const T da = aty - atc;
+      Lt += dx * dx * itx;
       RH += fabs(dx * dh);
       RB += fabs(dx * da);
     }
   }
   double v[4] = {double(Lt), 0.0, double(RH), double(RB)};
   block_reduce_store<4>(v, 0u, d.part + P_TR_C * kMaxBlocks);
+}
+
+template <typename T, int G, bool COND>
+__global__ void __launch_bounds__(kBlock) k_cols(Dev<T> d, int nb_r) {
+  if (d.st->status != ST_RUNNING) {
+    stop_loop<COND>(d.hw, d.hc);
+    return;
+  }
+  cols_phase<T, G, G>(d, d.st);
   if (arrive_last(d.ctr)) {
     decide_body<COND>(d.st, d.part, nb_r, gridDim.x, d.hw, d.hc);
     if (threadIdx.x == 0) d.ctr[0] = 0u;
   }
+}
+
+// ===========================================================================
+// Panel stream of the persistent loop.  The rows of one or two CSR matrices
+// with the same row set are cut into panels of kBlock rows; each block takes
+// panels blockIdx.x, blockIdx.x + gridDim.x, ...  For each panel one thread
+// issues bulk copies of the panel's column-index and value ranges (rounded
+// to 16 bytes) into one of two shared-memory stages while the block works on
+// the other stage, so the matrix stream runs ahead of the arithmetic instead
+// of behind a chain of dependent loads.  In a stage, the block first forms
+// the products a_k x[col_k] over the panel's entries (coalesced, many
+// independent gathers per thread, written in place of the values), then
+// thread t sums the products of row panel + t in entry order.  A panel whose
+// entries do not fit a stage is read directly from global memory (same
+// order).  Per row: pre(r, valid) runs before the wait (its loads overlap the
+// copies) and returns a context; post(r, valid, ctx, sums) runs after.
+// ===========================================================================
+constexpr int kStageEntries = 3072;  // entries (index + value) per stage, all matrices of a panel
+template <typename T>
+constexpr unsigned stage_bytes() {
+  return kStageEntries * (4u + (unsigned)sizeof(T));
+}
+// Dynamic shared memory of the persistent loop: two stages.  (Shared memory
+// taken here is L1 capacity lost to the in-flight loads of every pass, so
+// the products are formed in place.)
+template <typename T>
+constexpr unsigned stream_smem_bytes() {
+  return 2 * stage_bytes<T>();
+}
+
+struct StreamCtl {
+  unsigned long long bar[2];
+  int base[2][2];  // per stage and matrix: first entry copied (multiple of 4)
+  int cnt[2][2];   // entries copied (multiple of 4)
+  int off[2][2];   // byte offset of the index array in the stage (values follow)
+  int fits[2];
+};
+
+__device__ __forceinline__ void stream_init(StreamCtl &ctl) {
+  if (threadIdx.x == 0) {
+    mbar_init(&ctl.bar[0], 1);
+    mbar_init(&ctl.bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+}
+
+// Row bounds of panel p (thread 0 loads them one panel ahead of the issue).
+template <typename T, int NM>
+__device__ __forceinline__ void panel_bounds(const Mat<T> *M, long long p, long long nrows, int *lo, int *hi) {
+  const long long r0 = p * kBlock;
+  const long long r1 = r0 + kBlock < nrows ? r0 + kBlock : nrows;
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    lo[m] = M[m].rp[r0];
+    hi[m] = M[m].rp[r1];
+  }
+}
+
+template <typename T, int NM>
+__device__ __forceinline__ void stream_issue(StreamCtl &ctl, unsigned char *buf, int st, const Mat<T> *M,
+                                             const int *lo, const int *hi) {
+  unsigned total = 0;
+  int a[NM], c[NM], o[NM];
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    a[m] = lo[m] & ~3;
+    c[m] = ((hi[m] + 3) & ~3) - a[m];
+    o[m] = (int)total;
+    total += (unsigned)c[m] * (4u + (unsigned)sizeof(T));
+  }
+  const int fits = total <= stage_bytes<T>() ? 1 : 0;
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    ctl.base[st][m] = a[m];
+    ctl.cnt[st][m] = c[m];
+    ctl.off[st][m] = o[m];
+  }
+  ctl.fits[st] = fits;
+  unsigned char *dst = buf + (size_t)st * stage_bytes<T>();
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(&ctl.bar[st], fits ? total : 0u);
+  if (fits) {
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      if (c[m] > 0) {
+        bulk_g2s(dst + o[m], M[m].ci + a[m], (unsigned)c[m] * 4u, &ctl.bar[st]);
+        bulk_g2s(dst + o[m] + 4 * c[m], M[m].val + a[m], (unsigned)c[m] * (unsigned)sizeof(T), &ctl.bar[st]);
+      }
+    }
+  }
+}
+
+template <typename T, int NM, typename Pre, typename Post>
+__device__ __forceinline__ bool stream_panels(StreamCtl &ctl, unsigned char *buf, unsigned &ph, unsigned *fault,
+                                              const Mat<T> *M, const T *const *gx, long long nrows, Pre pre,
+                                              Post post) {
+  const long long np = (nrows + kBlock - 1) / kBlock;
+  long long p = blockIdx.x;
+  if (p >= np) return true;
+  int nlo[NM], nhi[NM];  // thread 0: bounds of the next panel to issue
+  if (threadIdx.x == 0) {
+    int lo[NM], hi[NM];
+    panel_bounds<T, NM>(M, p, nrows, lo, hi);
+    stream_issue<T, NM>(ctl, buf, 0, M, lo, hi);
+    if (p + gridDim.x < np) panel_bounds<T, NM>(M, p + gridDim.x, nrows, nlo, nhi);
+  }
+  // Row-local work of a panel (its row bounds and pre()) is done one panel
+  // ahead, so that its loads are in flight while the current panel waits for
+  // its copy and forms its products.
+  int rb[NM], re[NM];
+  auto load_rows = [&](long long q, int *b, int *e) {
+    const long long r = q * kBlock + threadIdx.x;
+    const bool v = q < np && r < nrows;
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      b[m] = v ? M[m].rp[r] : 0;
+      e[m] = v ? M[m].rp[r + 1] : 0;
+    }
+    return pre(r, v);
+  };
+  auto ctx = load_rows(p, rb, re);
+  for (int k = 0; p < np; ++k, p += gridDim.x) {
+    const int st = k & 1;
+    const long long pn = p + gridDim.x;
+    if (pn < np && threadIdx.x == 0) {
+      stream_issue<T, NM>(ctl, buf, st ^ 1, M, nlo, nhi);
+      if (pn + gridDim.x < np) panel_bounds<T, NM>(M, pn + gridDim.x, nrows, nlo, nhi);
+    }
+    int rbn[NM], ren[NM];
+    auto ctxn = load_rows(pn, rbn, ren);
+    const long long r = p * kBlock + threadIdx.x;
+    const bool valid = r < nrows;
+    if (!mbar_wait_block(&ctl.bar[st], (ph >> st) & 1u, fault)) {
+      // Leave no copy of the next panel in flight (bounded wait).
+      if (pn < np && threadIdx.x == 0)
+        for (unsigned it = 0; it <= kSpinLimitTx && !mbar_test(&ctl.bar[st ^ 1], (ph >> (st ^ 1)) & 1u); ++it)
+          __nanosleep(32);
+      return false;
+    }
+    ph ^= 1u << st;
+    T sum[NM];
+    if (ctl.fits[st]) {
+      unsigned char *sb = buf + (size_t)st * stage_bytes<T>();
+      // Products in batches of kGB entries per thread: all index and value
+      // reads and all gathers of a batch are issued before its stores.
+      constexpr int kGB = 8;
+#pragma unroll
+      for (int m = 0; m < NM; ++m) {
+        const int cnt = ctl.cnt[st][m];
+        const int *sci = reinterpret_cast<const int *>(sb + ctl.off[st][m]);
+        T *sv = reinterpret_cast<T *>(sb + ctl.off[st][m] + 4 * cnt);
+        const T *g = gx[m];
+        for (int e0 = threadIdx.x; e0 < cnt; e0 += kGB * kBlock) {
+          int ci[kGB];
+          T a[kGB], xg[kGB];
+#pragma unroll
+          for (int u = 0; u < kGB; ++u) {
+            const int e = e0 + u * kBlock;
+            ci[u] = e < cnt ? sci[e] : 0;
+            a[u] = e < cnt ? sv[e] : T(0);
+          }
+#pragma unroll
+          for (int u = 0; u < kGB; ++u) xg[u] = __ldcg(g + ci[u]);
+#pragma unroll
+          for (int u = 0; u < kGB; ++u) {
+            const int e = e0 + u * kBlock;
+            if (e < cnt) sv[e] = a[u] * xg[u];
+          }
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < NM; ++m) {
+        const int cnt = ctl.cnt[st][m];
+        const T *sv = reinterpret_cast<const T *>(sb + ctl.off[st][m] + 4 * cnt);
+        const int b0 = ctl.base[st][m];
+        T a = T(0);
+        for (int k2 = rb[m]; k2 < re[m]; ++k2) a += sv[k2 - b0];
+        sum[m] = a;
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < NM; ++m) {
+        T a = T(0);
+        for (int k2 = rb[m]; k2 < re[m]; ++k2) a += M[m].val[k2] * __ldcg(gx[m] + M[m].ci[k2]);
+        sum[m] = a;
+      }
+    }
+    post(r, valid, ctx, sum);
+    ctx = ctxn;
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      rb[m] = rbn[m];
+      re[m] = ren[m];
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// Row pass of the persistent loop: the per-row arithmetic of rows_phase with
+// (A x_tr) from the panel stream.
+template <typename T>
+__device__ __forceinline__ bool rows_phase_stream(const Dev<T> &d, const DevState *st, StreamCtl &ctl,
+                                                  unsigned char *buf, unsigned &ph, unsigned *fault) {
+  const int cur = st->cur, nx = 1 - cur, a0 = st->acur, acc = st->accepted;
+  const double t = (double)st->t;
+  const T alpha = T(2.0 / (t + 2.0)), oma = T(1) - alpha;
+  const T beta = T(t / (t + 1.0));
+  const T sct = T(st->kappa / st->omega), sce = T(st->kappa * st->omega);
+  const T ap = T(st->alpha_acc), omap = T(1) - ap;
+  T Lt = T(0), Le = T(0), RH = T(0), RB = T(0);
+  struct Ctx {
+    T y, r, rt, stv, ds, bw, etj, hpj, sig, itr, ie;
+  };
+  const Mat<T> M[1] = {d.A};
+  const T *gx[1] = {d.x[nx]};
+  const bool ok = stream_panels<T, 1>(
+      ctl, buf, ph, fault, M, gx, d.m,
+      [&](long long j, bool valid) {
+        // Every load of the row first, then the arithmetic, then the stores
+        // (a store to a T array would otherwise hold back later loads).
+        Ctx c = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+        if (valid) {
+          const bool ineq = j >= d.mE;
+          c.y = d.y[cur][j];
+          c.r = d.r[cur][j];
+          T rb = d.rbar[a0][j];
+          const T yb0 = acc ? d.ybar[a0][j] : T(0);
+          c.sig = T(d.sig[j]);
+          const T tr = d.taur[j], qr = d.qr[j];
+          c.bw = d.Bw[cur][j];
+          c.etj = d.eta[j];
+          c.hpj = d.hp[j];
+          c.itr = d.itaur[j];
+          c.ie = d.ieta[j];
+          T s = T(0), sb0 = T(0), ts = T(0), qs = T(0), ls = T(0), us = T(0), its = T(0);
+          if (ineq) {
+            s = d.s[cur][j];
+            if (acc) sb0 = d.sbar[a0][j];
+            ts = d.taus[j];
+            qs = d.qs[j];
+            ls = d.ls[j];
+            us = d.us[j];
+            its = d.itaus[j];
+          }
+          if (acc) {  // running averages of the previous acceptance
+            rb = omap * rb + ap * c.r;
+            d.rbar[a0 ^ 1][j] = rb;
+            d.ybar[a0 ^ 1][j] = omap * yb0 + ap * c.y;
+            if (ineq) d.sbar[a0 ^ 1][j] = omap * sb0 + ap * s;
+          }
+          c.rt = c.r - (sct * tr) * (qr + c.sig * (oma * rb + alpha * c.r) + c.y);
+          d.r[nx][j] = c.rt;
+          if (ineq) {
+            c.stv = clampv<T>(s - (sct * ts) * (qs + c.y), ls, us);
+            d.s[nx][j] = c.stv;
+            c.ds = c.stv - s;
+            Lt += c.ds * c.ds * its;
+          }
+        }
+        return c;
+      },
+      [&](long long j, bool valid, const Ctx &c, const T *sum) {
+        if (!valid) return;
+        T bwt = sum[0] - c.rt;
+        if (j >= d.mE) bwt -= c.stv;
+        const T yt = c.y + (sce * c.etj) * (c.hpj - bwt - beta * (bwt - c.bw));
+        d.Bw[nx][j] = bwt;
+        d.y[nx][j] = yt;
+        const T dr = c.rt - c.r, dyv = yt - c.y;
+        Lt += dr * dr * c.itr;
+        Le += dyv * dyv * c.ie;
+        RH += fabs(dr * c.sig * dr);
+        RB += fabs(c.ds * dyv) + fabs(dr * dyv);
+      });
+  double v[4] = {double(Lt), double(Le), double(RH), double(RB)};
+  block_reduce_store<4>(v, 0u, d.part + P_TR_R * kMaxBlocks);
+  return ok;
+}
+
+// Column pass of the persistent loop: H x_tr and A' y_tr from the panel
+// stream (both matrices in the same panel), then the per-variable terms.
+template <typename T>
+__device__ __forceinline__ bool cols_phase_stream(const Dev<T> &d, const DevState *st, StreamCtl &ctl,
+                                                  unsigned char *buf, unsigned &ph, unsigned *fault) {
+  const int cur = st->cur, nx = 1 - cur;
+  T Lt = T(0), RH = T(0), RB = T(0);
+  struct Ctx {
+    T xti, xci, hxc, atc, itx;
+  };
+  const Mat<T> M[2] = {d.H, d.At};
+  const T *gx[2] = {d.x[nx], d.y[nx]};
+  const bool ok = stream_panels<T, 2>(
+      ctl, buf, ph, fault, M, gx, d.n,
+      [&](long long i, bool valid) {
+        Ctx c = {T(0), T(0), T(0), T(0), T(0)};
+        if (valid) {
+          c.xti = d.x[nx][i];
+          c.xci = d.x[cur][i];
+          c.hxc = d.Hx[cur][i];
+          c.atc = d.Aty[cur][i];
+          c.itx = d.itaux[i];
+        }
+        return c;
+      },
+      [&](long long i, bool valid, const Ctx &c, const T *sum) {
+        if (!valid) return;
+        d.Hx[nx][i] = sum[0];
+        d.Aty[nx][i] = sum[1];
+        const T dx = c.xti - c.xci;
+        const T dh = sum[0] - c.hxc;
+        const T da = sum[1] - c.atc;
+        Lt += dx * dx * c.itx;
+        RH += fabs(dx * dh);
+        RB += fabs(dx * da);
+      });
+  double v[4] = {double(Lt), 0.0, double(RH), double(RB)};
+  block_reduce_store<4>(v, 0u, d.part + P_TR_C * kMaxBlocks);
+  return ok;
+}
+
+// Persistent trial loop (one cooperative launch): primal, rows and columns of
+// each trial are separated by grid barriers, and the last block to reach the
+// third barrier takes the acceptance decision (decide_body) before releasing
+// the others, which then reload the scalar state.  The loop leaves when the
+// solve stops, a periodic check is due (the check kernels follow this launch)
+// or the launch's trial allowance (slot_left) is used up; it does not start
+// while a check is pending (the check kernels clear check_due).  All blocks
+// take the same branches (the state is block-uniform), so every barrier is
+// reached by every block.  Partial sums use this grid's size for both passes.
+template <typename T>
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 2) k_trials(Dev<T> d) {
+  __shared__ DevState S;
+  __shared__ StreamCtl ctl;
+  extern __shared__ __align__(128) unsigned char stage_buf[];
+  unsigned *bar = d.ctr + kCtrBar;
+  unsigned *fault = bar + kBarFault;
+  unsigned ph = 0u;  // parity of the next wait on each stage
+  stream_init(ctl);
+  state_load(S, d.st);
+  const int nb = gridDim.x;
+  // Block 0 times each pass: its own work, then its wait at the barrier
+  // (imbalance across blocks plus the barrier itself; the last one includes
+  // the acceptance decision).
+  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+  unsigned long long tp[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+  unsigned long long tk = timer ? global_ns() : 0ull;
+  auto lap = [&](int k) {
+    if (timer) {
+      const unsigned long long t = global_ns();
+      tp[k] += t - tk;
+      tk = t;
+    }
+  };
+  while (S.status == ST_RUNNING && S.slot_left > 0 && !S.check_due) {
+    primal_phase<T>(d, &S);
+    lap(0);
+    if (!grid_sync(bar)) return;
+    lap(1);
+    if (!rows_phase_stream<T>(d, &S, ctl, stage_buf, ph, fault)) return;
+    lap(2);
+    if (!grid_sync(bar)) return;
+    lap(3);
+    if (!cols_phase_stream<T>(d, &S, ctl, stage_buf, ph, fault)) return;
+    lap(4);
+    if (!grid_sync(bar, [&] { decide_body<false>(d.st, d.part, nb, nb, 0, 0); })) return;
+    state_load(S, d.st);
+    lap(5);
+  }
+  if (timer && d.ptime)
+    for (int k = 0; k < 6; ++k) d.ptime[k] += tp[k];
 }
 
 // Acceptance decision (single block, deterministic order).  On acceptance the
@@ -292,8 +766,18 @@ __device__ void decide_body(DevState *stg, const double *part, int nb_r, int nb_
   __shared__ DevState S;
   state_load(S, stg);
   double a[4], b[4];
-  final_reduce<4>(part + P_TR_R * kMaxBlocks, nb_r, 0u, a);
-  final_reduce<4>(part + P_TR_C * kMaxBlocks, nb_c, 0u, b);
+  if (nb_r == nb_c) {
+    // Row and column partials of one grid (rows 0-3 and 4-7): one pass.
+    double ab[8];
+    final_reduce<8>(part + P_TR_R * kMaxBlocks, nb_r, 0u, ab);
+    for (int k = 0; k < 4; ++k) {
+      a[k] = ab[k];
+      b[k] = ab[4 + k];
+    }
+  } else {
+    final_reduce<4>(part + P_TR_R * kMaxBlocks, nb_r, 0u, a);
+    final_reduce<4>(part + P_TR_C * kMaxBlocks, nb_c, 0u, b);
+  }
   if (threadIdx.x == 0) {
     DevState *st = &S;
     // Commit the averages materialised by this slot's primal / row kernels.
@@ -560,10 +1044,14 @@ __device__ void check_final_body(DevState *stg, const double *part, int nb_r, in
     double q[16];
     for (int k = 0; k < 16; ++k) q[k] = ((CK_MAXMASK >> k) & 1u) ? fmax(a[k], b[k]) : a[k] + b[k];
     for (int k = 0; k < 16; ++k) st->chk[k] = q[k];
-    // The averages of this trial's acceptance were materialised by the check kernels.
+    // The averages of this trial's acceptance were materialised by the check
+    // kernels.  The check is consumed here (a repeated launch of the check
+    // kernels without a trial in between does nothing); the restart itself is
+    // applied by k_check_apply on restart_flag.
     st->acur ^= st->accepted;
     st->accepted = 0;
     st->restart_flag = 0;
+    st->check_due = 0;
     const double dta = st->dta, dtr = st->dtr;
     const double spc = fmax(1.0, q[1]), sdc = fmax(1.0, q[3]);
     const double spa = fmax(1.0, q[9]), sda = fmax(1.0, q[11]);
@@ -612,7 +1100,7 @@ __device__ void check_final_body(DevState *stg, const double *part, int nb_r, in
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_check_apply(Dev<T> d) {
   const DevState *st = d.st;
-  if (!(st->check_due && st->restart_flag)) return;
+  if (!st->restart_flag) return;
   const int cur = st->cur, ab = st->acur;
   const bool ua = st->restart_use_avg;
   PDNQP_GRID_STRIDE(i, d.n) {

@@ -52,6 +52,8 @@ struct Params {
   long long iter_budget = 4000000000000000000LL;
   int g_rows = 0, g_cols = 0;  // entries per lane per CSR-stream chunk (0 = from the mean row length)
   int cond_graph = 1;          // 1: device-driven WHILE/IF graph; 0: unrolled slots (profilable)
+  int persistent = 1;          // 1: persistent cooperative trial loop (when supported)
+  int loop_blocks_per_sm = 0;  // blocks per SM of that loop (0: as many as fit)
 };
 
 struct Result {
@@ -61,6 +63,10 @@ struct Result {
   double seconds = 0, obj = 0;
   long long launches = 0;
   double inner_seconds = 0, setup_seconds = 0;
+  double loop_seconds = 0;
+  long long loop_trials = 0;
+  int loop_blocks = 0;
+  double loop_phase_seconds[6] = {0, 0, 0, 0, 0, 0};
 };
 
 class SolverBase {

@@ -51,8 +51,11 @@ class Solver : public SolverBase {
     if (gexec_) cudaGraphExecDestroy(gexec_);
     for (cudaEvent_t e : replay_ev_)
       if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : loop_ev_)
+      if (e) cudaEventDestroy(e);
     for (void *p : allocs_) cudaFree(p);
     if (hst_) cudaFreeHost(hst_);
+    if (hfault_) cudaFreeHost(hfault_);
     if (own_stream_) cudaStreamDestroy(s_);
   }
 
@@ -181,16 +184,20 @@ class Solver : public SolverBase {
 
  private:
   // ------------------------------------------------------------- helpers
+  // Every array carries kPad zeroed elements past its end: the bulk copies of
+  // the panel stream round their ranges up to 16 bytes and may read them.
+  static constexpr size_t kPad = 4;
   template <typename U>
   int dalloc(U **p, size_t count) {
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(U));
+    cudaError_t e = cudaMalloc(&q, (std::max<size_t>(count, 1) + kPad) * sizeof(U));
     if (e != cudaSuccess) {
       last_err_ = std::string("cudaMalloc: ") + cudaGetErrorString(e);
       return PDNQP_ERR_OOM;
     }
     allocs_.push_back(q);
     *p = (U *)q;
+    PDNQP_CK(cudaMemsetAsync((char *)q + count * sizeof(U), 0, kPad * sizeof(U), s_));
     return 0;
   }
   template <typename U>
@@ -229,6 +236,8 @@ class Solver : public SolverBase {
     nnzH_ = P.q_ci.size();
     PDNQP_TRY(dalloc(&st_, 1));
     PDNQP_CK(cudaMallocHost(&hst_, sizeof(DevState)));
+    PDNQP_CK(cudaMallocHost(&hfault_, sizeof(unsigned)));
+    *hfault_ = 0u;
     PDNQP_TRY(dalloc(&part_, (size_t)kMaxPartials * kMaxBlocks));
     PDNQP_TRY(dalloc(&dred_, 128));
     hred_.resize(128);
@@ -479,8 +488,10 @@ class Solver : public SolverBase {
     d.sig = sig_;
     d.part = part_;
     d.st = st_;
-    PDNQP_TRY(dalloc(&d.ctr, 4));
-    PDNQP_CK(cudaMemsetAsync(d.ctr, 0, 4 * sizeof(unsigned), s_));
+    PDNQP_TRY(dalloc(&d.ctr, kCtrWords));
+    PDNQP_CK(cudaMemsetAsync(d.ctr, 0, kCtrWords * sizeof(unsigned), s_));
+    PDNQP_TRY(dalloc(&d.ptime, 8));
+    PDNQP_CK(cudaMemsetAsync(d.ptime, 0, 8 * sizeof(unsigned long long), s_));
     d.hw = 0;
     d.hc = 0;
     PDNQP_CK(cudaGetLastError());
@@ -519,6 +530,44 @@ class Solver : public SolverBase {
   void launch_slot() {
     launch_trial();
     launch_check_group();
+  }
+  // Persistent trial loop: one cooperative launch per slot, grid = the
+  // co-resident block count (capped by the work), each launch bracketed by a
+  // pair of events so the loop's device time is measured on its own stream.
+  int coop_grid(int bps) {
+    if (coop_key_ == bps) return coop_nb_;
+    coop_key_ = bps;
+    coop_nb_ = 0;
+    int dev = 0, sms = 0, can = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&can, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !can) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    const int smem = (int)stream_smem_bytes<T>();
+    if (cudaFuncSetAttribute(k_trials<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trials<T>, kBlock, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    if (bps > 0) per_sm = std::min(per_sm, bps);
+    const int work = std::max(nb_rows(), nb_cols());
+    coop_nb_ = std::max(0, std::min(std::min(per_sm * sms, kMaxBlocks), work));
+    return coop_nb_;
+  }
+  int launch_trials_persistent(int nb, int slot) {
+    if (!loop_ev_[2 * slot]) {
+      PDNQP_CK(cudaEventCreate(&loop_ev_[2 * slot]));
+      PDNQP_CK(cudaEventCreate(&loop_ev_[2 * slot + 1]));
+    }
+    PDNQP_CK(cudaEventRecord(loop_ev_[2 * slot], s_));
+    void *args[] = {(void *)&d_};
+    PDNQP_CK(cudaLaunchCooperativeKernel((const void *)k_trials<T>, dim3(nb), dim3(kBlock), args,
+                                         stream_smem_bytes<T>(), s_));
+    PDNQP_CK(cudaEventRecord(loop_ev_[2 * slot + 1], s_));
+    return 0;
   }
   void launch_check(int mode) {
     with_G(gA_, [&](auto GG) { k_check_rows<T, decltype(GG)::value><<<nb_rows(), kBlock, 0, s_>>>(d_, mode); });
@@ -742,13 +791,50 @@ class Solver : public SolverBase {
 
   int read_state(DevState *S) {
     PDNQP_CK(cudaMemcpyAsync(hst_, st_, sizeof(DevState), cudaMemcpyDeviceToHost, s_));
+    PDNQP_CK(cudaMemcpyAsync(hfault_, d_.ctr + kCtrBar + kBarFault, sizeof(unsigned), cudaMemcpyDeviceToHost, s_));
     PDNQP_CK(cudaStreamSynchronize(s_));
     *S = *hst_;
+    if (*hfault_) {
+      // A grid barrier of the persistent loop gave up waiting: the launch ended
+      // early and the iterates are not usable.
+      cudaMemsetAsync(d_.ctr, 0, kCtrWords * sizeof(unsigned), s_);
+      cudaStreamSynchronize(s_);
+      last_err_ = "persistent trial loop: grid barrier timed out";
+      return PDNQP_ERR_CUDA;
+    }
     return 0;
   }
 
   // Runs graph chunks until the device status leaves RUNNING.
   int run_until_stop(const Params &prm, DevState *S, double t0) {
+    const int nbp = prm.persistent ? coop_grid(prm.loop_blocks_per_sm) : 0;
+    if (nbp > 0) {
+      // Persistent loop: batches of slots [trial loop, check rows, check cols
+      // (+ decisions), check apply]; a batch runs at most `per` trials, after
+      // which the host reads the state once.
+      const long long kc = std::max<long long>(1, prm.k_chk);
+      const long long per = std::max<long long>(prm.chunk, 8 * kc);
+      const int R = (int)std::min<long long>(kMaxLoopSlots, per / kc + 1);
+      for (;;) {
+        k_loop_begin<<<1, 1, 0, s_>>>(st_, per);
+        for (int r = 0; r < R; ++r) {
+          PDNQP_TRY(launch_trials_persistent(nbp, r));
+          launch_check_group();
+        }
+        PDNQP_CK(cudaGetLastError());
+        launches_ += 1 + 4LL * R;
+        const long long tr_before = hst_->trials;
+        PDNQP_TRY(read_state(S));
+        for (int r = 0; r < R; ++r) {
+          float ms = 0.f;
+          PDNQP_CK(cudaEventElapsedTime(&ms, loop_ev_[2 * r], loop_ev_[2 * r + 1]));
+          loop_seconds_ += 1e-3 * ms;
+        }
+        loop_trials_ += S->trials - tr_before;
+        if (S->status != ST_RUNNING) return 0;
+        if (seconds_since(t0) > prm.time_limit) return 1;
+      }
+    }
     PDNQP_TRY(build_graph(prm.chunk, prm.cond_graph));
     long long tr0 = -1, ac0 = 0;
     for (;;) {
@@ -827,6 +913,9 @@ class Solver : public SolverBase {
       gamma_pending_ = 0;
     }
     launches_ = 0;
+    loop_seconds_ = 0.0;
+    loop_trials_ = 0;
+    PDNQP_CK(cudaMemsetAsync(d_.ptime, 0, 8 * sizeof(unsigned long long), s_));
     double t_setup = 0.0, t_inner = 0.0;
     apply_g(prm);
     PDNQP_TRY(start_point(prm));
@@ -917,6 +1006,14 @@ class Solver : public SolverBase {
     res_.launches = launches_;
     res_.inner_seconds = t_inner;
     res_.setup_seconds = t_setup;
+    res_.loop_seconds = loop_seconds_;
+    res_.loop_trials = loop_trials_;
+    res_.loop_blocks = coop_nb_;
+    {
+      unsigned long long pt[8];
+      PDNQP_CK(cudaMemcpy(pt, d_.ptime, sizeof(pt), cudaMemcpyDeviceToHost));
+      for (int k = 0; k < 6; ++k) res_.loop_phase_seconds[k] = 1e-9 * (double)pt[k];
+    }
     solved_once_ = true;
     return status;
   }
@@ -1006,6 +1103,12 @@ class Solver : public SolverBase {
   Dev<T> d_{};
   cudaGraphExec_t gexec_ = nullptr;
   cudaEvent_t replay_ev_[2] = {nullptr, nullptr};
+  static constexpr int kMaxLoopSlots = 32;
+  cudaEvent_t loop_ev_[2 * kMaxLoopSlots] = {};
+  double loop_seconds_ = 0.0;  // device time of the persistent trial-loop launches
+  long long loop_trials_ = 0;  // trials they ran
+  int coop_key_ = -1, coop_nb_ = 0;
+  unsigned *hfault_ = nullptr;
   float last_replay_ms_ = 0.f;
   int graph_chunk_ = 0;
   bool use_cond_ = true;  // device-driven WHILE/IF graph (else unrolled slots)

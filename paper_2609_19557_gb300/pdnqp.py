@@ -39,7 +39,9 @@ class pdnqp_residuals(C.Structure):
                 ("trials", C.c_int64), ("restarts", C.c_int64), ("kkt_passes", C.c_int64),
                 ("solve_seconds", C.c_double), ("gamma", C.c_double), ("lambda_min", C.c_double),
                 ("obj", C.c_double), ("kernel_launches", C.c_int64),
-                ("inner_seconds", C.c_double), ("setup_seconds", C.c_double)]
+                ("inner_seconds", C.c_double), ("setup_seconds", C.c_double),
+                ("loop_seconds", C.c_double), ("loop_trials", C.c_int64), ("loop_blocks", C.c_int64),
+                ("loop_phase_seconds", C.c_double * 6)]
 
 
 class pdnqp_device_csr(C.Structure):
@@ -172,7 +174,9 @@ def pdnqp_get(h: Handle):
     y = np.zeros(h.m)
     r = pdnqp_residuals()
     _check(h.ptr, load().pdnqp_get(h.ptr, x.ctypes.data, y.ctypes.data if h.m else None, C.byref(r)))
-    return x, y, {f[0]: getattr(r, f[0]) for f in pdnqp_residuals._fields_}
+    out = {f[0]: getattr(r, f[0]) for f in pdnqp_residuals._fields_}
+    out["loop_phase_seconds"] = list(out["loop_phase_seconds"])
+    return x, y, out
 
 
 def pdnqp_set_start(h: Handle, x0=None, y0=None):
