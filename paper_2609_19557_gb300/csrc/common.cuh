@@ -184,38 +184,30 @@ __device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned pari
       : "memory");
   return ok != 0u;
 }
-// Bounded wait for the phase with the given parity, by thread 0 for its block:
-// the result is block-uniform (every thread returns it).  On success every
-// thread also observes the completed phase itself (immediately), which makes
-// the copied bytes visible to it.  On a timeout the fault flag is set and the
-// copies in flight get a second bounded wait before the block gives up, so no
-// copy is left writing into shared memory of a block that has left.
-__device__ __forceinline__ bool mbar_wait_block(unsigned long long *bar, unsigned parity, unsigned *fault) {
-  __shared__ int ok;
-  if (threadIdx.x == 0) {
-    int r = 0;
+// Bounded wait of one warp for the phase with the given parity: lane 0 polls
+// (and every 64 polls looks at the fault flag), the result is warp-uniform,
+// and on success every lane observes the completed phase itself, which makes
+// the copied bytes visible to it.  Returns false on a timeout (the fault flag
+// is then set) or when another warp has already set the fault flag.
+__device__ __forceinline__ bool mbar_wait_warp(unsigned long long *bar, unsigned parity, unsigned *fault) {
+  int r = 0;
+  if ((threadIdx.x & 31) == 0) {
     for (unsigned it = 0; it <= kSpinLimitTx; ++it) {
       if (mbar_test(bar, parity)) {
         r = 1;
         break;
       }
+      if ((it & 63u) == 63u && ld_acquire_gpu(fault) != 0u) break;
       __nanosleep(32);
     }
-    if (!r) {
-      atomicExch(fault, 1u);
-      for (unsigned it = 0; it <= kSpinLimitTx; ++it) {
-        if (mbar_test(bar, parity)) break;
-        __nanosleep(32);
-      }
-    }
-    ok = r;
+    if (!r) atomicExch(fault, 1u);
   }
-  __syncthreads();
-  const bool r = ok != 0;
+  r = __shfl_sync(0xffffffffu, r, 0);
   if (r)
     for (unsigned it = 0; it <= kSpinLimitTx && !mbar_test(bar, parity); ++it) {
     }
-  return r;
+  __syncwarp();
+  return r != 0;
 }
 
 // Device-wide nanosecond timer (phase timing of the persistent loop).

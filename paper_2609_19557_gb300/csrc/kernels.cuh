@@ -407,6 +407,7 @@ constexpr unsigned stream_smem_bytes() {
 
 struct StreamCtl {
   unsigned long long bar[2];
+  int done[2];     // per stage: warps finished with the panel in it
   int base[2][2];  // per stage and matrix: first entry copied (multiple of 4)
   int cnt[2][2];   // entries copied (multiple of 4)
   int off[2][2];   // byte offset of the index array in the stage (values follow)
@@ -468,112 +469,150 @@ __device__ __forceinline__ void stream_issue(StreamCtl &ctl, unsigned char *buf,
   }
 }
 
-template <typename T, int NM, typename Pre, typename Post>
+// Warps work through the panels independently: warp w owns rows 32w..32w+31
+// of every panel, waits for the panel's copy on the stage's mbarrier, forms
+// the products of its own entry ranges (contiguous slices of the stage) and
+// the row sums, and reports on the stage's counter; the last warp to finish
+// with a stage refills it with the panel two ahead.  Per panel a warp makes a
+// single round of dependent memory accesses: load(r) issues the row-local
+// loads before the wait, the gathers of all matrices go out in one batch,
+// and finish(r, raw, sums) does all the arithmetic and the stores at the end.
+// The only block-wide barriers are at the start and end of the pass.  On a
+// fault (a copy that never lands) the warps run out the loop without
+// touching the stages, the copies in flight get a bounded wait, and the pass
+// returns false.
+template <typename T, int NM, int GB, typename Load, typename Finish>
 __device__ __forceinline__ bool stream_panels(StreamCtl &ctl, unsigned char *buf, unsigned &ph, unsigned *fault,
-                                              const Mat<T> *M, const T *const *gx, long long nrows, Pre pre,
-                                              Post post) {
+                                              const Mat<T> *M, const T *const *gx, long long nrows, Load load,
+                                              Finish finish) {
+  constexpr int kWarps = kBlock / 32;
   const long long np = (nrows + kBlock - 1) / kBlock;
-  long long p = blockIdx.x;
-  if (p >= np) return true;
-  int nlo[NM], nhi[NM];  // thread 0: bounds of the next panel to issue
+  const long long p0 = blockIdx.x, nb = gridDim.x;
+  if (p0 >= np) return true;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
+    ctl.done[0] = 0;
+    ctl.done[1] = 0;
     int lo[NM], hi[NM];
-    panel_bounds<T, NM>(M, p, nrows, lo, hi);
+    panel_bounds<T, NM>(M, p0, nrows, lo, hi);
     stream_issue<T, NM>(ctl, buf, 0, M, lo, hi);
-    if (p + gridDim.x < np) panel_bounds<T, NM>(M, p + gridDim.x, nrows, nlo, nhi);
+    if (p0 + nb < np) {
+      panel_bounds<T, NM>(M, p0 + nb, nrows, lo, hi);
+      stream_issue<T, NM>(ctl, buf, 1, M, lo, hi);
+    }
   }
-  // Row-local work of a panel (its row bounds and pre()) is done one panel
-  // ahead, so that its loads are in flight while the current panel waits for
-  // its copy and forms its products.
-  int rb[NM], re[NM];
-  auto load_rows = [&](long long q, int *b, int *e) {
-    const long long r = q * kBlock + threadIdx.x;
-    const bool v = q < np && r < nrows;
-#pragma unroll
-    for (int m = 0; m < NM; ++m) {
-      b[m] = v ? M[m].rp[r] : 0;
-      e[m] = v ? M[m].rp[r + 1] : 0;
-    }
-    return pre(r, v);
-  };
-  auto ctx = load_rows(p, rb, re);
-  for (int k = 0; p < np; ++k, p += gridDim.x) {
-    const int st = k & 1;
-    const long long pn = p + gridDim.x;
-    if (pn < np && threadIdx.x == 0) {
-      stream_issue<T, NM>(ctl, buf, st ^ 1, M, nlo, nhi);
-      if (pn + gridDim.x < np) panel_bounds<T, NM>(M, pn + gridDim.x, nrows, nlo, nhi);
-    }
-    int rbn[NM], ren[NM];
-    auto ctxn = load_rows(pn, rbn, ren);
+  __syncthreads();
+  bool ok = true;
+  for (long long k = 0, p = p0; p < np; ++k, p += nb) {
+    const int st = (int)(k & 1);
     const long long r = p * kBlock + threadIdx.x;
     const bool valid = r < nrows;
-    if (!mbar_wait_block(&ctl.bar[st], (ph >> st) & 1u, fault)) {
-      // Leave no copy of the next panel in flight (bounded wait).
-      if (pn < np && threadIdx.x == 0)
-        for (unsigned it = 0; it <= kSpinLimitTx && !mbar_test(&ctl.bar[st ^ 1], (ph >> (st ^ 1)) & 1u); ++it)
-          __nanosleep(32);
-      return false;
-    }
-    ph ^= 1u << st;
-    T sum[NM];
-    if (ctl.fits[st]) {
-      unsigned char *sb = buf + (size_t)st * stage_bytes<T>();
-      // Products in batches of kGB entries per thread: all index and value
-      // reads and all gathers of a batch are issued before its stores.
-      constexpr int kGB = 8;
-#pragma unroll
-      for (int m = 0; m < NM; ++m) {
-        const int cnt = ctl.cnt[st][m];
-        const int *sci = reinterpret_cast<const int *>(sb + ctl.off[st][m]);
-        T *sv = reinterpret_cast<T *>(sb + ctl.off[st][m] + 4 * cnt);
-        const T *g = gx[m];
-        for (int e0 = threadIdx.x; e0 < cnt; e0 += kGB * kBlock) {
-          int ci[kGB];
-          T a[kGB], xg[kGB];
-#pragma unroll
-          for (int u = 0; u < kGB; ++u) {
-            const int e = e0 + u * kBlock;
-            ci[u] = e < cnt ? sci[e] : 0;
-            a[u] = e < cnt ? sv[e] : T(0);
-          }
-#pragma unroll
-          for (int u = 0; u < kGB; ++u) xg[u] = __ldcg(g + ci[u]);
-#pragma unroll
-          for (int u = 0; u < kGB; ++u) {
-            const int e = e0 + u * kBlock;
-            if (e < cnt) sv[e] = a[u] * xg[u];
-          }
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int m = 0; m < NM; ++m) {
-        const int cnt = ctl.cnt[st][m];
-        const T *sv = reinterpret_cast<const T *>(sb + ctl.off[st][m] + 4 * cnt);
-        const int b0 = ctl.base[st][m];
-        T a = T(0);
-        for (int k2 = rb[m]; k2 < re[m]; ++k2) a += sv[k2 - b0];
-        sum[m] = a;
-      }
-    } else {
-#pragma unroll
-      for (int m = 0; m < NM; ++m) {
-        T a = T(0);
-        for (int k2 = rb[m]; k2 < re[m]; ++k2) a += M[m].val[k2] * __ldcg(gx[m] + M[m].ci[k2]);
-        sum[m] = a;
-      }
-    }
-    post(r, valid, ctx, sum);
-    ctx = ctxn;
+    int rb[NM], re[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
-      rb[m] = rbn[m];
-      re[m] = ren[m];
+      rb[m] = valid ? M[m].rp[r] : 0;
+      re[m] = valid ? M[m].rp[r + 1] : 0;
     }
-    __syncthreads();
+    const auto raw = load(r, valid);
+    // This warp's rows: [rw, rw + 32) clipped to nrows.
+    const long long rw = p * kBlock + 32 * w;
+    const int last = rw < nrows ? (int)((nrows - 1 - rw) < 31 ? (nrows - 1 - rw) : 31) : -1;
+    T sum[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) sum[m] = T(0);
+    if (ok) ok = mbar_wait_warp(&ctl.bar[st], (ph >> st) & 1u, fault);
+    ph ^= 1u << st;
+    if (ok && last >= 0) {
+      if (ctl.fits[st]) {
+        unsigned char *sb = buf + (size_t)st * stage_bytes<T>();
+        int wb[NM], we[NM], b0[NM];
+        const int *sci[NM];
+        T *sv[NM];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+          const int cnt = ctl.cnt[st][m];
+          b0[m] = ctl.base[st][m];
+          sci[m] = reinterpret_cast<const int *>(sb + ctl.off[st][m]);
+          sv[m] = reinterpret_cast<T *>(sb + ctl.off[st][m] + 4 * cnt);
+          // The warp's entries [wb, we) (rows of invalid lanes are empty).
+          wb[m] = __shfl_sync(0xffffffffu, rb[m], 0) - b0[m];
+          we[m] = __shfl_sync(0xffffffffu, re[m], last) - b0[m];
+        }
+        // Products in batches of GB entries per lane and matrix: all index
+        // and value reads and all gathers of a batch (every matrix) are
+        // issued before its stores.
+        for (int j0 = lane;; j0 += GB * 32) {
+          bool more = false;
+#pragma unroll
+          for (int m = 0; m < NM; ++m) more |= wb[m] + j0 < we[m];
+          if (!__any_sync(0xffffffffu, more)) break;
+          int ci[NM][GB];
+          T a[NM][GB], xg[NM][GB];
+#pragma unroll
+          for (int m = 0; m < NM; ++m)
+#pragma unroll
+            for (int u = 0; u < GB; ++u) {
+              const int e = wb[m] + j0 + u * 32;
+              ci[m][u] = e < we[m] ? sci[m][e] : 0;
+              a[m][u] = e < we[m] ? sv[m][e] : T(0);
+            }
+#pragma unroll
+          for (int m = 0; m < NM; ++m)
+#pragma unroll
+            for (int u = 0; u < GB; ++u) xg[m][u] = __ldcg(gx[m] + ci[m][u]);
+#pragma unroll
+          for (int m = 0; m < NM; ++m)
+#pragma unroll
+            for (int u = 0; u < GB; ++u) {
+              const int e = wb[m] + j0 + u * 32;
+              if (e < we[m]) sv[m][e] = a[m][u] * xg[m][u];
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+          T a = T(0);
+          for (int k2 = rb[m]; k2 < re[m]; ++k2) a += sv[m][k2 - b0[m]];
+          sum[m] = a;
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+          T a = T(0);
+          for (int k2 = rb[m]; k2 < re[m]; ++k2) a += M[m].val[k2] * __ldcg(gx[m] + M[m].ci[k2]);
+          sum[m] = a;
+        }
+      }
+    }
+    // Done with the stage: the last warp refills it with the panel two ahead.
+    // The fences on both sides of the counter order every warp's reads and
+    // in-place writes of the stage before the refill's copy.
+    __syncwarp();
+    bool refill = false;
+    if (ok && lane == 0) {
+      __threadfence_block();
+      refill = atomicAdd(&ctl.done[st], 1) == kWarps - 1;
+    }
+    if (refill) {
+      __threadfence_block();
+      ctl.done[st] = 0;
+      const long long p2 = p + 2 * nb;
+      if (p2 < np) {
+        int lo[NM], hi[NM];
+        panel_bounds<T, NM>(M, p2, nrows, lo, hi);
+        stream_issue<T, NM>(ctl, buf, st, M, lo, hi);
+      }
+    }
+    finish(r, valid, raw, sum);
   }
-  return true;
+  __syncthreads();
+  if (!ok && threadIdx.x == 0) {
+    // Bounded wait for copies that may still be in flight.
+    for (int s2 = 0; s2 < 2; ++s2)
+      for (unsigned it = 0; it <= kSpinLimitTx && !mbar_test(&ctl.bar[s2], (ph >> s2) & 1u); ++it) __nanosleep(32);
+  }
+  __syncthreads();
+  return ok;
 }
 
 // Row pass of the persistent loop: the per-row arithmetic of rows_phase with
@@ -588,69 +627,71 @@ __device__ __forceinline__ bool rows_phase_stream(const Dev<T> &d, const DevStat
   const T sct = T(st->kappa / st->omega), sce = T(st->kappa * st->omega);
   const T ap = T(st->alpha_acc), omap = T(1) - ap;
   T Lt = T(0), Le = T(0), RH = T(0), RB = T(0);
-  struct Ctx {
-    T y, r, rt, stv, ds, bw, etj, hpj, sig, itr, ie;
+  struct Raw {
+    T y, r, rb, yb, tr, qr, bw, eta, hp, itr, ie, s, sb, ts, qs, ls, us, its;
+    double sig;
   };
   const Mat<T> M[1] = {d.A};
   const T *gx[1] = {d.x[nx]};
-  const bool ok = stream_panels<T, 1>(
+  const bool ok = stream_panels<T, 1, 8>(
       ctl, buf, ph, fault, M, gx, d.m,
       [&](long long j, bool valid) {
-        // Every load of the row first, then the arithmetic, then the stores
-        // (a store to a T array would otherwise hold back later loads).
-        Ctx c = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+        Raw c;
+        memset(&c, 0, sizeof(c));
         if (valid) {
-          const bool ineq = j >= d.mE;
           c.y = d.y[cur][j];
           c.r = d.r[cur][j];
-          T rb = d.rbar[a0][j];
-          const T yb0 = acc ? d.ybar[a0][j] : T(0);
-          c.sig = T(d.sig[j]);
-          const T tr = d.taur[j], qr = d.qr[j];
+          c.rb = d.rbar[a0][j];
+          if (acc) c.yb = d.ybar[a0][j];
+          c.sig = d.sig[j];
+          c.tr = d.taur[j];
+          c.qr = d.qr[j];
           c.bw = d.Bw[cur][j];
-          c.etj = d.eta[j];
-          c.hpj = d.hp[j];
+          c.eta = d.eta[j];
+          c.hp = d.hp[j];
           c.itr = d.itaur[j];
           c.ie = d.ieta[j];
-          T s = T(0), sb0 = T(0), ts = T(0), qs = T(0), ls = T(0), us = T(0), its = T(0);
-          if (ineq) {
-            s = d.s[cur][j];
-            if (acc) sb0 = d.sbar[a0][j];
-            ts = d.taus[j];
-            qs = d.qs[j];
-            ls = d.ls[j];
-            us = d.us[j];
-            its = d.itaus[j];
-          }
-          if (acc) {  // running averages of the previous acceptance
-            rb = omap * rb + ap * c.r;
-            d.rbar[a0 ^ 1][j] = rb;
-            d.ybar[a0 ^ 1][j] = omap * yb0 + ap * c.y;
-            if (ineq) d.sbar[a0 ^ 1][j] = omap * sb0 + ap * s;
-          }
-          c.rt = c.r - (sct * tr) * (qr + c.sig * (oma * rb + alpha * c.r) + c.y);
-          d.r[nx][j] = c.rt;
-          if (ineq) {
-            c.stv = clampv<T>(s - (sct * ts) * (qs + c.y), ls, us);
-            d.s[nx][j] = c.stv;
-            c.ds = c.stv - s;
-            Lt += c.ds * c.ds * its;
+          if (j >= d.mE) {
+            c.s = d.s[cur][j];
+            if (acc) c.sb = d.sbar[a0][j];
+            c.ts = d.taus[j];
+            c.qs = d.qs[j];
+            c.ls = d.ls[j];
+            c.us = d.us[j];
+            c.its = d.itaus[j];
           }
         }
         return c;
       },
-      [&](long long j, bool valid, const Ctx &c, const T *sum) {
+      [&](long long j, bool valid, const Raw &c, const T *sum) {
         if (!valid) return;
-        T bwt = sum[0] - c.rt;
-        if (j >= d.mE) bwt -= c.stv;
-        const T yt = c.y + (sce * c.etj) * (c.hpj - bwt - beta * (bwt - c.bw));
+        const bool ineq = j >= d.mE;
+        T rb = c.rb;
+        if (acc) {  // running averages of the previous acceptance
+          rb = omap * rb + ap * c.r;
+          d.rbar[a0 ^ 1][j] = rb;
+          d.ybar[a0 ^ 1][j] = omap * c.yb + ap * c.y;
+          if (ineq) d.sbar[a0 ^ 1][j] = omap * c.sb + ap * c.s;
+        }
+        const T sig = T(c.sig);
+        const T rt = c.r - (sct * c.tr) * (c.qr + sig * (oma * rb + alpha * c.r) + c.y);
+        d.r[nx][j] = rt;
+        T bwt = sum[0] - rt, ds = T(0);
+        if (ineq) {
+          const T stv = clampv<T>(c.s - (sct * c.ts) * (c.qs + c.y), c.ls, c.us);
+          d.s[nx][j] = stv;
+          ds = stv - c.s;
+          Lt += ds * ds * c.its;
+          bwt -= stv;
+        }
+        const T yt = c.y + (sce * c.eta) * (c.hp - bwt - beta * (bwt - c.bw));
         d.Bw[nx][j] = bwt;
         d.y[nx][j] = yt;
-        const T dr = c.rt - c.r, dyv = yt - c.y;
+        const T dr = rt - c.r, dyv = yt - c.y;
         Lt += dr * dr * c.itr;
         Le += dyv * dyv * c.ie;
-        RH += fabs(dr * c.sig * dr);
-        RB += fabs(c.ds * dyv) + fabs(dr * dyv);
+        RH += fabs(dr * sig * dr);
+        RB += fabs(ds * dyv) + fabs(dr * dyv);
       });
   double v[4] = {double(Lt), double(Le), double(RH), double(RB)};
   block_reduce_store<4>(v, 0u, d.part + P_TR_R * kMaxBlocks);
@@ -664,15 +705,15 @@ __device__ __forceinline__ bool cols_phase_stream(const Dev<T> &d, const DevStat
                                                   unsigned char *buf, unsigned &ph, unsigned *fault) {
   const int cur = st->cur, nx = 1 - cur;
   T Lt = T(0), RH = T(0), RB = T(0);
-  struct Ctx {
+  struct Raw {
     T xti, xci, hxc, atc, itx;
   };
   const Mat<T> M[2] = {d.H, d.At};
   const T *gx[2] = {d.x[nx], d.y[nx]};
-  const bool ok = stream_panels<T, 2>(
+  const bool ok = stream_panels<T, 2, 6>(
       ctl, buf, ph, fault, M, gx, d.n,
       [&](long long i, bool valid) {
-        Ctx c = {T(0), T(0), T(0), T(0), T(0)};
+        Raw c = {T(0), T(0), T(0), T(0), T(0)};
         if (valid) {
           c.xti = d.x[nx][i];
           c.xci = d.x[cur][i];
@@ -682,7 +723,7 @@ __device__ __forceinline__ bool cols_phase_stream(const Dev<T> &d, const DevStat
         }
         return c;
       },
-      [&](long long i, bool valid, const Ctx &c, const T *sum) {
+      [&](long long i, bool valid, const Raw &c, const T *sum) {
         if (!valid) return;
         d.Hx[nx][i] = sum[0];
         d.Aty[nx][i] = sum[1];
