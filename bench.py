@@ -17,6 +17,7 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -44,8 +45,9 @@ def parse():
     p.add_argument("--ttk", type=float, default=0.0, help="also time a solve to rel-KKT 1e-4 (cap in seconds)")
     p.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU (oracle) baseline leg")
-    p.add_argument("--graph", default="cond", choices=["cond", "unrolled"],
-                   help="inner loop as a conditional (WHILE/IF) graph, or unrolled slots (inspectable by ncu)")
+    p.add_argument("--loop", default="persistent", choices=["persistent", "cond", "unrolled"],
+                   help="inner loop: one persistent cooperative launch per check period (default), or a CUDA graph "
+                        "with conditional WHILE/IF nodes, or unrolled graph slots")
     p.add_argument("--n", type=int, default=1_000_000)
     p.add_argument("--m", type=int, default=500_000)
     return p.parse_args()
@@ -117,6 +119,26 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def set_loop(P, h, loop):
+    P.pdnqp_set_param(h, "persistent", 1 if loop == "persistent" else 0)
+    P.pdnqp_set_param(h, "cond_graph", 1 if loop == "cond" else 0)
+
+
+def aggregate(ws, dt, iters, device):
+    """Whole-job figures of a timed region: the slowest rank's time and the sum
+    of the units all ranks processed (replicas: no data-path collective; this
+    is the only exchange, after the timed region)."""
+    if ws <= 1:
+        return dt, iters
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(dt)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(iters)], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(c.item()))
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -142,7 +164,7 @@ def run_native(args):
     stream = torch.cuda.current_stream()
     h = P.create_from_instance(inst, precision=args.precision, stream=stream.cuda_stream)
     P.pdnqp_set_param(h, "iter_budget", args.budget)
-    P.pdnqp_set_param(h, "cond_graph", 1 if args.graph == "cond" else 0)
+    set_loop(P, h, args.loop)
 
     def barrier():
         if ws > 1:
@@ -158,6 +180,7 @@ def run_native(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     iters = 0
     launches = 0
+    loop_s, loop_trials, loop_launches, blocks = 0.0, 0, 0, 0
     barrier()
     ev0.record(stream)
     for _ in range(args.steps):
@@ -165,39 +188,43 @@ def run_native(args):
         _, _, r = P.pdnqp_get(h)
         iters += r["inner_iters"]
         launches += r["kernel_launches"]
+        loop_s += r["loop_seconds"]
+        loop_trials += r["loop_trials"]
+        loop_launches += r["loop_launches"]
+        blocks = r["loop_blocks"]
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
     dt = ev0.elapsed_time(ev1) / 1e3
-    t_max = dt
-    it_all = iters
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dt], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        c = torch.tensor([float(iters)], device="cuda")
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        it_all = int(c.item())
+    t_max, it_all = aggregate(ws, dt, iters, "cuda")
     value = it_all / t_max
 
-    # Dominant kernel: fused Q / A^T SpMV + acceptance terms, replayed on the same stream.
+    # Dominant kernel: the persistent trial loop (k_trials), timed live inside
+    # the timed region by CUDA events around each of its launches on this
+    # stream; algorithmic bytes per trial from the library (every array once
+    # per pass, gathers served from L2).
     peak, peak_src = measured_peaks()
-    kb = P.pdnqp_kernel_bytes(h, 0)
-    P.pdnqp_replay_kernel(h, 0, 5)
-    reps = 50
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    P.pdnqp_replay_kernel(h, 0, reps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    kdur = e0.elapsed_time(e1) / 1e3 / reps
-    achieved = kb / kdur / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", f"traffic_cols_fp{args.precision}.json")
-    if os.path.exists(tr_path):
-        traffic = json.load(open(tr_path)).get("bytes_per_launch")
+    roof = None
+    if loop_trials > 0 and loop_s > 0:
+        bpt = P.pdnqp_kernel_bytes(h, 5)
+        achieved = bpt * loop_trials / loop_s / 1e9
+        per_launch = loop_trials / max(1, loop_launches)
+        traffic = None
+        tr_path = os.path.join(ROOT, "profiles", f"traffic_trials_fp{args.precision}.json")
+        if os.path.exists(tr_path):
+            # Counters of one ncu capture, valid only while the kernel sources
+            # are the ones they were taken on.
+            tj = json.load(open(tr_path))
+            hsh = hashlib.sha256()
+            for f in tj.get("source_files", []):
+                hsh.update(open(os.path.join(ROOT, f), "rb").read())
+            if tj.get("source_sha256") == hsh.hexdigest() and tj.get("dram_bytes_per_trial"):
+                traffic = tj["dram_bytes_per_trial"] * per_launch
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "k_trials (persistent trial loop: primal, row and column passes, "
+                "acceptance decision)", "peak_source": peak_src,
+                "algorithmic_bytes_per_trial": bpt, "trials_per_launch": per_launch,
+                "us_per_trial": 1e6 * loop_s / loop_trials, "blocks": blocks}
 
     # End to end through the public API with host buffers: create (H2D of the
     # problem) + solve + get (D2H of x, y) inside the timed region.
@@ -212,26 +239,21 @@ def run_native(args):
     for _ in range(e2e_steps):
         h2 = P.create_from_instance(inst, precision=args.precision, stream=stream.cuda_stream)
         P.pdnqp_set_param(h2, "iter_budget", args.budget)
+        set_loop(P, h2, args.loop)
         P.pdnqp_solve(h2, 1e-4, 1e-4)
         x, y, r2 = P.pdnqp_get(h2)
         e2e_iters += r2["inner_iters"]
         h2.close()
     barrier()
     e2e_dt = time.perf_counter() - t0
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_dt], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_dt = float(t.item())
-        c = torch.tensor([float(e2e_iters)], device="cuda")
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        e2e_iters = int(c.item())
+    e2e_dt, e2e_iters = aggregate(ws, e2e_dt, e2e_iters, "cuda")
 
     # Plain FP64 form on the same GPU (the comparison the metric names).
     compare = None
     if not args.no_compare and args.precision != 64:
         h64 = P.create_from_instance(inst, precision=64, stream=stream.cuda_stream)
         P.pdnqp_set_param(h64, "iter_budget", args.budget)
+        set_loop(P, h64, args.loop)
         P.pdnqp_solve(h64, 1e-4, 1e-4)
         torch.cuda.synchronize()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -267,14 +289,12 @@ def run_native(args):
             "dtype": "f32+f64" if args.precision == 32 else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": args.n, "m": args.m, "step": f"pdnqp_solve with {args.budget} "
                        "accepted inner iterations", "l2": "inputs larger than L2 (no flush)",
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "loop": args.loop,
                        "precision": "FP32-bulk" if args.precision == 32 else "plain FP64"},
             "e2e": {"value": e2e_iters / e2e_dt, "unit": "iters/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_cols (Q and A^T SpMV + acceptance)",
-                         "peak_source": peak_src, "kernel_us": kdur * 1e6},
+            "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clk,
         }

@@ -99,6 +99,7 @@ typedef struct {
   double loop_seconds;       /* device time (CUDA events) of the persistent trial-loop launches; 0 in graph modes */
   int64_t loop_trials;       /* trials run inside those launches */
   int64_t loop_blocks;       /* blocks of the persistent launch (0: graph modes) */
+  int64_t loop_launches;     /* persistent trial-loop launches (including ones that found nothing to do) */
   double loop_phase_seconds[6]; /* device time of their passes as seen by block 0 (globaltimer): primal work,
                                    primal barrier wait, row work, row barrier wait, column work, column barrier
                                    wait + acceptance decision */
@@ -198,9 +199,11 @@ PDNQP_API int pdnqp_debug_inner(pdnqp_t *h, int n_ckpt, const int64_t *ckpt, dou
 PDNQP_API int pdnqp_replay_kernel(pdnqp_t *h, int which, int reps);
 PDNQP_API double pdnqp_replay_last_ms(const pdnqp_t *h);
 
-/* Algorithmic (compulsory) DRAM bytes of one launch of the kernel `which`
- * (same numbering as pdnqp_replay_kernel) and of one accepted iteration
- * (which = -1), for the roofline. */
+/* Algorithmic (compulsory) DRAM bytes, for the roofline: of one launch of
+ * the kernel `which` (same numbering as pdnqp_replay_kernel; 3: the average
+ * materialisation), of one trial of the persistent trial loop (which = 5:
+ * primal, row and column passes, every array once per pass, gathers served
+ * from L2), or of the graph-mode kernels of one trial together (which = -1). */
 PDNQP_API int pdnqp_kernel_bytes(const pdnqp_t *h, int which, double *bytes);
 
 /* ------------------------------------------------------------------------ */

@@ -337,6 +337,7 @@ int pdnqp_get(const pdnqp_t *h, double *x, double *y, pdnqp_residuals *r) {
     r->loop_seconds = R.loop_seconds;
     r->loop_trials = R.loop_trials;
     r->loop_blocks = R.loop_blocks;
+    r->loop_launches = R.loop_launches;
     for (int k = 0; k < 6; ++k) r->loop_phase_seconds[k] = R.loop_phase_seconds[k];
   }
   return 0;
@@ -448,7 +449,7 @@ int pdnqp_replay_kernel(pdnqp_t *h, int which, int reps) {
 double pdnqp_replay_last_ms(const pdnqp_t *h) { return h ? h->solver->last_replay_ms() : -1.0; }
 
 int pdnqp_kernel_bytes(const pdnqp_t *h, int which, double *bytes) {
-  if (!h || !bytes || which < -1 || which > 3) return fail(nullptr, PDNQP_ERR_ARG, "bad arguments");
+  if (!h || !bytes || which < -1 || which > 5 || which == 4) return fail(nullptr, PDNQP_ERR_ARG, "bad arguments");
   *bytes = h->solver->kernel_bytes(which);
   return 0;
 }

@@ -66,6 +66,7 @@ struct Result {
   double loop_seconds = 0;
   long long loop_trials = 0;
   int loop_blocks = 0;
+  long long loop_launches = 0;
   double loop_phase_seconds[6] = {0, 0, 0, 0, 0, 0};
 };
 

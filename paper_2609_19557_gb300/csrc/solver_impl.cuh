@@ -175,6 +175,21 @@ class Solver : public SolverBase {
     const double primal = 9 * v * n;
     // k_average: reads/writes xbar, Hxbar (read x, Hx), ybar, rbar (+ sbar), (read y, r, s).
     const double avg = 6 * v * n + 6 * v * m + 3 * v * mI;
+    if (which == 5) {
+      // One trial of the persistent loop (k_trials) after an accepted trial,
+      // each array counted once per pass (gathers assumed served from L2):
+      // primal: reads x, Hx, Hxbar, xbar, qx, A'y, taux, lx, ux; writes x_tr,
+      //   Hxbar', xbar'.
+      const double p5 = 12 * v * n;
+      // rows: A; gathers x_tr; reads y, r, rbar, ybar, taur, qr, Bw, eta, hp,
+      //   itaur, ieta and sig (FP64) per row, s, sbar, taus, qs, ls, us,
+      //   itaus per inequality row; writes rbar', ybar', r, Bw, y (+ sbar', s).
+      const double r5 = mat_a + v * n + m * (16 * v + 8) + mI * 9 * v;
+      // cols: H, A^T; gathers x_tr (also read per row) and y_tr; reads x,
+      //   Hx, A'y, taux; writes Hx_tr, A'y_tr.
+      const double c5 = mat_h + mat_at + 7 * v * n + v * m;
+      return p5 + r5 + c5;
+    }
     if (which == 0) return cols;
     if (which == 1) return rows;
     if (which == 2) return primal;
@@ -823,6 +838,7 @@ class Solver : public SolverBase {
         }
         PDNQP_CK(cudaGetLastError());
         launches_ += 1 + 4LL * R;
+        loop_launches_ += R;
         const long long tr_before = hst_->trials;
         PDNQP_TRY(read_state(S));
         for (int r = 0; r < R; ++r) {
@@ -915,6 +931,7 @@ class Solver : public SolverBase {
     launches_ = 0;
     loop_seconds_ = 0.0;
     loop_trials_ = 0;
+    loop_launches_ = 0;
     PDNQP_CK(cudaMemsetAsync(d_.ptime, 0, 8 * sizeof(unsigned long long), s_));
     double t_setup = 0.0, t_inner = 0.0;
     apply_g(prm);
@@ -1009,6 +1026,7 @@ class Solver : public SolverBase {
     res_.loop_seconds = loop_seconds_;
     res_.loop_trials = loop_trials_;
     res_.loop_blocks = coop_nb_;
+    res_.loop_launches = loop_launches_;
     {
       unsigned long long pt[8];
       PDNQP_CK(cudaMemcpy(pt, d_.ptime, sizeof(pt), cudaMemcpyDeviceToHost));
@@ -1106,6 +1124,7 @@ class Solver : public SolverBase {
   static constexpr int kMaxLoopSlots = 32;
   cudaEvent_t loop_ev_[2 * kMaxLoopSlots] = {};
   double loop_seconds_ = 0.0;  // device time of the persistent trial-loop launches
+  long long loop_launches_ = 0;
   long long loop_trials_ = 0;  // trials they ran
   int coop_key_ = -1, coop_nb_ = 0;
   unsigned *hfault_ = nullptr;

@@ -41,6 +41,7 @@ class pdnqp_residuals(C.Structure):
                 ("obj", C.c_double), ("kernel_launches", C.c_int64),
                 ("inner_seconds", C.c_double), ("setup_seconds", C.c_double),
                 ("loop_seconds", C.c_double), ("loop_trials", C.c_int64), ("loop_blocks", C.c_int64),
+                ("loop_launches", C.c_int64),
                 ("loop_phase_seconds", C.c_double * 6)]
 
 
