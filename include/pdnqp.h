@@ -103,6 +103,8 @@ typedef struct {
   double loop_phase_seconds[6]; /* device time of their passes as seen by block 0 (globaltimer): primal work,
                                    primal barrier wait, row work, row barrier wait, column work, column barrier
                                    wait + acceptance decision */
+  int64_t ctrl_used;         /* outer iterations whose rho_in / primal weight came from the learned controller */
+  int64_t ctrl_fallbacks;    /* outer iterations where the paper's rule overrode it (fallback) */
 } pdnqp_residuals;
 
 /* Creation options (pdnqp_create uses precision = PDNQP_FP64, device = current,
@@ -269,6 +271,76 @@ PDNQP_API const char *pdnqp_kkt_last_error(void);
  * Arguments, layout and return codes are those of pdnqp_kkt_residuals. */
 PDNQP_API int pdnqp_kkt_residuals_noalloc(const pdnqp_device_problem *P, const double *x, const double *y,
                                           double *out, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Learned controller (MLP 16 -> 64 -> 64 -> 2, GELU hidden layers).         */
+/* ------------------------------------------------------------------------ */
+/* The network proposes the inner tolerance factor rho_in (in place of Eq.
+ * inner-tolerance-factor) and the primal weight carried into the next inner
+ * solve; the paper's rules remain the fallback (pdnqp_set_controller).
+ * Parameters are one flat array in this order, row-major (out x in):
+ * W1[64][16], b1[64], W2[64][64], b2[64], W3[2][64], b3[2] (5,378 values,
+ * pdnqp_mlp_param_count()).  Inference uses BF16 weights (uint16 bit
+ * patterns) and FP32 arithmetic.  All pointers below are DEVICE pointers,
+ * work is enqueued on `stream` (NULL = legacy default stream) and the calls
+ * return without waiting; they return 0, PDNQP_ERR_ARG (message from
+ * pdnqp_mlp_last_error) or PDNQP_ERR_CUDA (launch failure). */
+PDNQP_API int pdnqp_mlp_param_count(void);
+/* y[batch][2] = MLP(x[batch][16]).  cache (batch x 128 floats, or NULL)
+ * receives the pre-activations of both hidden layers for pdnqp_mlp_backward. */
+PDNQP_API int pdnqp_mlp_forward(const uint16_t *w_bf16, const float *x, int batch, float *y, float *cache,
+                                void *stream);
+/* Weighted squared error L = sum_s w_s |y_s - t_s|^2 / sum_s w_s (weight NULL:
+ * all 1) into *loss (device float, or NULL) and dL/dy into dy[batch][2]. */
+PDNQP_API int pdnqp_mlp_wmse(const float *y, const float *target, const float *weight, int batch, float *dy,
+                             float *loss, void *stream);
+/* grad[5378] = dL/dtheta for dL/dy = dy, through the BF16 weights, using the
+ * cache of the forward pass.  scratch holds ceil(batch / 16) x 5378 floats
+ * of per-block partial gradients (batch <= 16384); the sum over blocks runs
+ * in a fixed order, so the result is deterministic. */
+PDNQP_API int pdnqp_mlp_backward(const uint16_t *w_bf16, const float *x, const float *cache, const float *dy,
+                                 int batch, float *grad, float *scratch, void *stream);
+/* One Adam step (bias-corrected, step >= 1) on the FP32 master weights w with
+ * moments m, v; also rewrites w_bf16 (round to nearest even). */
+PDNQP_API int pdnqp_mlp_adam(float *w, uint16_t *w_bf16, const float *grad, float *m, float *v, int step, float lr,
+                             float beta1, float beta2, float eps, void *stream);
+/* w_bf16[i] = round-to-nearest-even(w[i]) for i < count. */
+PDNQP_API int pdnqp_mlp_to_bf16(const float *w, uint16_t *w_bf16, int count, void *stream);
+PDNQP_API const char *pdnqp_mlp_last_error(void);
+
+/* Installs the controller's weights on a handle (weights: HOST pointer to
+ * pdnqp_mlp_param_count() FP32 values, copied and rounded to BF16 on the
+ * device; NULL removes them).  With the parameter `controller` = 1 and
+ * weights installed, every outer iteration evaluates the network on the
+ * features below; its two outputs correct the rules' action a_rule (trace
+ * columns 19-20): a = a_rule + out, rho_in = rho_in_min + (rho_in_max -
+ * rho_in_min) * sigmoid(a[0]) and the next inner solve's starting primal
+ * weight omega * exp(clamp(a[1], -1, 1)) (a network with a zero last layer
+ * reproduces the rules).  The paper's rules stay the fallback and
+ * the judge: an outer iteration after one whose network proposal increased
+ * the relative KKT residual uses the rules (Eq. inner-tolerance-factor, the
+ * carried primal weight); so do iterations without weights or with
+ * controller = 0.  The parameter ctrl_explore > 0 adds Gaussian noise of that
+ * standard deviation to the actions taken (seeded by ctrl_seed), for
+ * generating training trajectories.  Returns 0 or a negative error code. */
+PDNQP_API int pdnqp_set_controller(pdnqp_t *h, const float *weights, int count);
+
+/* Trace of the last pdnqp_solve, one row of PDNQP_TRACE_COLS doubles per
+ * outer iteration that reached the tolerance update: [0] outer index k,
+ * [1] relative KKT residual (original data) after inner solve k, [2] accepted
+ * inner iterations of inner solve k, [3..18] the 16 controller features,
+ * [19..20] the rules' action (logit of the rho_in fraction, log primal-weight
+ * ratio = 0), [21..22] the action taken, [23] 1 if the network chose it.
+ * Features: log10 of the relative primal and dual residuals (original data),
+ * log10 of the scaled primal ratio r_p/s_p and of the scaled dual residual,
+ * the changes of the first two since the previous outer iteration, log10 of
+ * the inner absolute tolerance, log10(1 + inner iterations) and log10(1 +
+ * restarts) of the inner solve, log10 of the primal weight and of gamma,
+ * log10 of the proximal movement |x - z| / gamma, the rules' rho_in and the
+ * ratio it is built from, log10(1 + k) and the penalty-growth flag.  Writes
+ * min(n, max_rows) rows to `rows` (host) and n to *n_rows. */
+#define PDNQP_TRACE_COLS 24
+PDNQP_API int pdnqp_get_trace(const pdnqp_t *h, double *rows, int64_t max_rows, int64_t *n_rows);
 
 #ifdef __cplusplus
 }

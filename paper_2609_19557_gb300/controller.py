@@ -1,0 +1,150 @@
+"""Learned inner-solve controller: trajectory generation, training on the GPU
+with the library's own MLP kernels, and evaluation against the paper's rules.
+
+The network (16 -> 64 -> 64 -> 2, GELU) maps the per-outer-iteration features
+of the solver trace (see pdnqp_get_trace in include/pdnqp.h) to a correction
+of the rules' action (logit of the rho_in fraction, log ratio of the next
+primal weight); with a zero last layer it reproduces the rules.  It is
+trained by reward-weighted regression on trajectories the method generates
+itself: the solver runs the paper's rules with Gaussian exploration noise on
+the actions, each action is scored by the progress it bought (decrease of
+log10 of the relative KKT residual per log10 of the inner iterations the next
+inner solve needed), and the network regresses onto the deviations from the
+rules that were taken, with weights exp(beta * standardised score).  Feature
+standardisation is folded into the first layer, so the solver feeds raw
+features.  In the solver the paper's rules stay the fallback and the judge
+(pdnqp_set_controller).
+
+    python -m paper_2609_19557_gb300.controller --train 200 --eval 8 --out weights.npy
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import instances as I
+from . import mlp_data as D
+from . import pdnqp as P
+
+F0, NF = 3, 16          # feature columns in the trace
+A_RULE, A_TAKEN = 19, 21  # the rules' action (19, 20) and the action taken (21, 22)
+
+
+def make_instance(seed: int, n: int) -> dict:
+    """The mid-size generator (power-law rows, free variables, equality rows) at n variables, m = n / 2."""
+    return I.mid_qp(seed, n=n, m=n // 2, replica_n=min(3000, n))
+
+
+def run(inst: dict, *, precision=32, eps=1e-4, controller=None, explore=0.0, seed=0, time_limit=60.0, stream=None):
+    h = P.create_from_instance(inst, precision=precision, stream=stream)
+    P.pdnqp_set_param(h, "time_limit", time_limit)
+    if controller is not None:
+        P.pdnqp_set_controller(h, controller)
+        P.pdnqp_set_param(h, "controller", 1)
+    if explore > 0:
+        P.pdnqp_set_param(h, "ctrl_explore", explore)
+        P.pdnqp_set_param(h, "ctrl_seed", seed)
+    t = time.perf_counter()
+    st = P.pdnqp_solve(h, eps, eps)
+    wall = time.perf_counter() - t
+    x, y, r = P.pdnqp_get(h)
+    tr = P.pdnqp_get_trace(h)
+    h.close()
+    return {"status": P.STATUS_NAMES[st], "outer": r["outer_iters"], "inner": r["inner_iters"],
+            "rel_kkt": r["rel_kkt"], "seconds": wall, "ctrl_used": r["ctrl_used"],
+            "ctrl_fallbacks": r["ctrl_fallbacks"], "x": x, "y": y}, tr
+
+
+def transitions(trace: np.ndarray):
+    """(features, action, score) of every action whose outcome the trace shows."""
+    out = []
+    for k in range(len(trace) - 1):
+        a, b = trace[k], trace[k + 1]
+        gain = np.log10(max(a[1], 1e-300)) - np.log10(max(b[1], 1e-300))
+        cost = np.log10(10.0 + b[2])
+        out.append((a[F0:F0 + NF], a[A_TAKEN:A_TAKEN + 2] - a[A_RULE:A_RULE + 2], gain / cost))
+    return out
+
+
+def train(feats, acts, scores, *, beta=1.0, epochs=3000, lr=3e-3, seed=0):
+    """Reward-weighted regression with the library's forward / backward / Adam
+    kernels; returns FP32 weights with the feature standardisation folded in."""
+    import torch
+    X = np.asarray(feats, dtype=np.float64)
+    A = np.asarray(acts, dtype=np.float32)
+    S = np.asarray(scores, dtype=np.float64)
+    mu, sd = X.mean(axis=0), X.std(axis=0)
+    sd[sd < 1e-6] = 1.0
+    Xn = ((X - mu) / sd).astype(np.float32)
+    z = (S - S.mean()) / (S.std() + 1e-12)
+    wt = np.exp(np.clip(beta * z, -3.0, 3.0)).astype(np.float32)
+    B = len(Xn)
+    w32 = D.init_weights(seed)
+    w32[D.N_PARAMS - D.N_OUT * D.N_HID - D.N_OUT:] = 0.0  # zero last layer: starts as the rules
+    w = torch.tensor(w32, device="cuda")
+    wb = torch.zeros(w32.size, dtype=torch.int16, device="cuda")
+    P.mlp_to_bf16(w, wb)
+    x, t, ww = (torch.tensor(v, device="cuda") for v in (Xn, A, wt))
+    y = torch.zeros((B, 2), device="cuda")
+    cache = torch.zeros((B, 128), device="cuda")
+    dy, loss = torch.zeros_like(y), torch.zeros(1, device="cuda")
+    m, v, grad = torch.zeros_like(w), torch.zeros_like(w), torch.zeros_like(w)
+    scratch = torch.zeros(((B + 15) // 16) * w.numel(), device="cuda")
+    hist = []
+    for step in range(1, epochs + 1):
+        P.mlp_forward(wb, x, y, cache)
+        P.mlp_wmse(y, t, ww, dy, loss)
+        P.mlp_backward(wb, x, cache, dy, grad, scratch)
+        P.mlp_adam(w, wb, grad, m, v, step, lr=lr)
+        if step == 1 or step % 500 == 0:
+            hist.append((step, loss.item()))
+    theta = w.cpu().numpy().astype(np.float64)
+    # Fold x_n = (x - mu) / sd into the first layer: W1' = W1 / sd, b1' = b1 - W1' mu.
+    n1 = D.N_HID * D.N_IN
+    W1 = theta[:n1].reshape(D.N_HID, D.N_IN) / sd
+    theta[:n1] = W1.ravel()
+    theta[n1:n1 + D.N_HID] -= W1 @ mu
+    return theta.astype(np.float32), hist
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=200, help="training trajectories")
+    ap.add_argument("--eval", type=int, default=8, help="fresh evaluation instances")
+    ap.add_argument("--n-min", type=int, default=10_000)
+    ap.add_argument("--n-max", type=int, default=50_000)
+    ap.add_argument("--explore", type=float, default=0.5)
+    ap.add_argument("--eps", type=float, default=1e-4)
+    ap.add_argument("--time-limit", type=float, default=60.0)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    P.load()
+    rng = np.random.default_rng(np.random.SeedSequence([2024, 7]))
+    data, t0 = [], time.perf_counter()
+    for i in range(a.train):
+        n = int(rng.integers(a.n_min, a.n_max + 1))
+        _, tr = run(make_instance(10_000 + i, n), eps=a.eps, explore=a.explore, seed=i, time_limit=a.time_limit)
+        data += transitions(tr)
+    gen_s = time.perf_counter() - t0
+    feats, acts, scores = zip(*data)
+    theta, hist = train(feats, acts, scores)
+    if a.out:
+        np.save(a.out, theta)
+    rows = []
+    for j in range(a.eval):
+        n = int(rng.integers(a.n_min, a.n_max + 1))
+        inst = make_instance(90_000 + j, n)
+        base, _ = run(inst, eps=a.eps, time_limit=a.time_limit)
+        ctrl, _ = run(inst, eps=a.eps, controller=theta, time_limit=a.time_limit)
+        rows.append({"n": n, **{f"rule_{k}": base[k] for k in ("status", "outer", "inner", "seconds", "rel_kkt")},
+                     **{f"mlp_{k}": ctrl[k] for k in ("status", "outer", "inner", "seconds", "rel_kkt",
+                                                      "ctrl_used", "ctrl_fallbacks")}})
+    print(json.dumps({"trajectories": a.train, "transitions": len(data), "generation_s": gen_s,
+                      "loss": hist, "eval": rows}, default=float))
+
+
+if __name__ == "__main__":
+    main()

@@ -338,6 +338,8 @@ int pdnqp_get(const pdnqp_t *h, double *x, double *y, pdnqp_residuals *r) {
     r->loop_trials = R.loop_trials;
     r->loop_blocks = R.loop_blocks;
     r->loop_launches = R.loop_launches;
+    r->ctrl_used = R.ctrl_used;
+    r->ctrl_fallbacks = R.ctrl_fallbacks;
     for (int k = 0; k < 6; ++k) r->loop_phase_seconds[k] = R.loop_phase_seconds[k];
   }
   return 0;
@@ -367,7 +369,8 @@ int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0) {
   X(rej_limit, i, 1.0, 1e9) X(kappa_shrink, d, 1e-6, 0.999999) X(delta_sigma, d, 1.0, 1e300)       \
   X(sigma_max, d, 1e-300, 1e300) X(tol_floor, d, 0.0, 1.0) X(chunk, i, 1.0, 65536.0)               \
   X(g_rows, i, 0.0, 16.0) X(g_cols, i, 0.0, 16.0) X(iter_budget, ll, 1.0, 4e18) X(cond_graph, i, 0.0, 1.0) \
-  X(persistent, i, 0.0, 1.0) X(loop_blocks_per_sm, i, 0.0, 32.0)
+  X(persistent, i, 0.0, 1.0) X(loop_blocks_per_sm, i, 0.0, 32.0) X(controller, i, 0.0, 1.0)             \
+  X(ctrl_explore, d, 0.0, 10.0) X(ctrl_seed, ll, 0.0, 9.2e18)
 
 int pdnqp_set_param(pdnqp_t *h, const char *name, double value) {
   if (!h || !name) return fail(h, PDNQP_ERR_ARG, "NULL handle or name");
@@ -451,6 +454,26 @@ double pdnqp_replay_last_ms(const pdnqp_t *h) { return h ? h->solver->last_repla
 int pdnqp_kernel_bytes(const pdnqp_t *h, int which, double *bytes) {
   if (!h || !bytes || which < -1 || which > 5 || which == 4) return fail(nullptr, PDNQP_ERR_ARG, "bad arguments");
   *bytes = h->solver->kernel_bytes(which);
+  return 0;
+}
+
+int pdnqp_set_controller(pdnqp_t *h, const float *weights, int count) {
+  if (!h) return fail(nullptr, PDNQP_ERR_ARG, "NULL handle");
+  if (weights && count != pdnqp_mlp_param_count())
+    return fail(h, PDNQP_ERR_ARG, "controller weights must have pdnqp_mlp_param_count() entries");
+  cudaSetDevice(h->device);
+  int rc = h->solver->set_controller(weights, weights ? count : 0);
+  if (rc < 0) return fail(h, rc, "pdnqp_set_controller: device error");
+  return 0;
+}
+
+int pdnqp_get_trace(const pdnqp_t *h, double *rows, int64_t max_rows, int64_t *n_rows) {
+  if (!h || !n_rows || max_rows < 0 || (max_rows > 0 && !rows)) return fail(nullptr, PDNQP_ERR_ARG, "bad arguments");
+  const std::vector<double> &t = h->solver->trace();
+  const int64_t n = (int64_t)(t.size() / PDNQP_TRACE_COLS);
+  *n_rows = n;
+  const int64_t k = n < max_rows ? n : max_rows;
+  for (int64_t i = 0; i < k * PDNQP_TRACE_COLS; ++i) rows[i] = t[(size_t)i];
   return 0;
 }
 

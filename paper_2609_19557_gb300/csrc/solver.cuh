@@ -54,6 +54,9 @@ struct Params {
   int cond_graph = 1;          // 1: device-driven WHILE/IF graph; 0: unrolled slots (profilable)
   int persistent = 1;          // 1: persistent cooperative trial loop (when supported)
   int loop_blocks_per_sm = 0;  // blocks per SM of that loop (0: as many as fit)
+  int controller = 0;          // 1: the learned controller proposes rho_in and the next primal weight
+  double ctrl_explore = 0.0;   // std. dev. of Gaussian noise added to the actions (trajectory generation)
+  long long ctrl_seed = 0;
 };
 
 struct Result {
@@ -67,6 +70,7 @@ struct Result {
   long long loop_trials = 0;
   int loop_blocks = 0;
   long long loop_launches = 0;
+  long long ctrl_used = 0, ctrl_fallbacks = 0;  // outer iterations driven by the network / by the fallback
   double loop_phase_seconds[6] = {0, 0, 0, 0, 0, 0};
 };
 
@@ -85,6 +89,9 @@ class SolverBase {
   virtual double lambda_min() const = 0;
   virtual void set_gamma(double g) = 0;
   virtual int64_t nnz_q() const = 0;
+  virtual int set_controller(const float *w, int count) = 0;
+  virtual const std::vector<double> &trace() const = 0;
+  virtual long long ctrl_fallbacks() const = 0;
 };
 
 SolverBase *make_solver_f64(cudaStream_t s);

@@ -19,6 +19,12 @@ namespace pdq {
     }                                                                             \
   } while (0)
 
+#define PDNQP_TRY(x)          \
+  do {                        \
+    int _r = (x);             \
+    if (_r < 0) return _r;    \
+  } while (0)
+
 // K = entries per lane per CSR-stream chunk (chunk = 32 K nonzeros per warp).
 // Kernels are instantiated for K in {4, 8, 16}; GroupIter kernels read it as
 // lanes per row.
@@ -70,6 +76,29 @@ class Solver : public SolverBase {
   double lambda_min() const override { return lam_min_; }
   int64_t nnz_q() const override { return nnzH_; }
   void set_gamma(double g) override { gamma_pending_ = g; }
+
+  // Learned controller: BF16 weights on the device (rounded there from the
+  // FP32 copy), evaluated once per outer iteration on the solve's stream.
+  int set_controller(const float *w, int count) override {
+    has_ctrl_ = false;
+    if (!w || count <= 0) return 0;
+    if (!ctrl_w_) {
+      PDNQP_TRY(dalloc(&ctrl_w32_, (size_t)count));
+      PDNQP_TRY(dalloc(&ctrl_w_, (size_t)count));
+      PDNQP_TRY(dalloc(&ctrl_x_, 16));
+      PDNQP_TRY(dalloc(&ctrl_y_, 2));
+    }
+    PDNQP_CK(cudaMemcpyAsync(ctrl_w32_, w, sizeof(float) * count, cudaMemcpyHostToDevice, s_));
+    if (pdnqp_mlp_to_bf16(ctrl_w32_, ctrl_w_, count, s_) != 0) {
+      last_err_ = std::string("controller weights: ") + pdnqp_mlp_last_error();
+      return PDNQP_ERR_CUDA;
+    }
+    PDNQP_CK(cudaStreamSynchronize(s_));
+    has_ctrl_ = true;
+    return 0;
+  }
+  const std::vector<double> &trace() const override { return trace_; }
+  long long ctrl_fallbacks() const override { return ctrl_fallbacks_; }
 
   int set_start(const double *x0, const double *lam0_int) override {
     // Stored in original coordinates / internal row order; applied at the next solve.
@@ -222,11 +251,6 @@ class Solver : public SolverBase {
     if (!h.empty()) PDNQP_CK(cudaMemcpyAsync(*p, h.data(), sizeof(U) * h.size(), cudaMemcpyHostToDevice, s_));
     return 0;
   }
-#define PDNQP_TRY(x)          \
-  do {                        \
-    int _r = (x);             \
-    if (_r < 0) return _r;    \
-  } while (0)
 
   int grid_n() const { return grid_for(n_, kBlock); }
   int grid_m() const { return grid_for(m_, kBlock); }
@@ -940,7 +964,13 @@ class Solver : public SolverBase {
     int status = PDNQP_ITER_LIMIT;
     long long k;
     double q[12];
+    trace_.clear();
+    ctrl_used_ = ctrl_fallbacks_ = 0;
+    bool ctrl_last = false;
+    double rel_prev = 0.0, f0_prev = 0.0, f1_prev = 0.0;
+    unsigned long long rng = (unsigned long long)prm.ctrl_seed * 0x9E3779B97F4A7C15ULL + 0x1234567ULL;
     for (k = 0; k < prm.k_out; ++k) {
+      const long long acc_before = accepted_, rst_before = restarts_;
       if (seconds_since(t0) > prm.time_limit) {
         status = PDNQP_TIME_LIMIT;
         break;
@@ -991,7 +1021,82 @@ class Solver : public SolverBase {
                                                     prm.delta_sigma, prm.sigma_max);
       // Eq. inner-tolerance-factor.
       const double ratio = rds > 0.0 ? std::min(1.0, (dxz / gamma_) / rds) : 1.0;
-      const double rho = prm.rho_in_max - (prm.rho_in_max - prm.rho_in_min) * ratio;
+      double rho = prm.rho_in_max - (prm.rho_in_max - prm.rho_in_min) * ratio;
+      {
+        // Learned controller (with the rules as fallback and judge) and the
+        // trace of this outer iteration.
+        const double rel_now = std::max(rpu / (1.0 + spu), rdu / (1.0 + sdu));
+        auto lg = [](double v) { return std::log10(std::max(v, 1e-300)); };
+        double f[16];
+        f[0] = lg(rpu / (1.0 + spu));
+        f[1] = lg(rdu / (1.0 + sdu));
+        f[2] = lg(rps / sps);
+        f[3] = lg(rds);
+        f[4] = trace_.empty() ? 0.0 : f[0] - f0_prev;
+        f[5] = trace_.empty() ? 0.0 : f[1] - f1_prev;
+        f[6] = lg(dta);
+        f[7] = std::log10(1.0 + (double)(accepted_ - acc_before));
+        f[8] = std::log10(1.0 + (double)(restarts_ - rst_before));
+        f[9] = lg(omega_);
+        f[10] = lg(gamma_);
+        f[11] = lg(dxz / gamma_);
+        f[12] = rho;
+        f[13] = ratio;
+        f[14] = std::log10(1.0 + (double)k);
+        f[15] = grow ? 1.0 : 0.0;
+        for (double &v : f) v = std::min(30.0, std::max(-30.0, v));
+        const double span = prm.rho_in_max - prm.rho_in_min;
+        double fr = span > 0.0 ? (rho - prm.rho_in_min) / span : 0.5;
+        fr = std::min(1.0 - 1e-3, std::max(1e-3, fr));
+        const double ar[2] = {std::log(fr / (1.0 - fr)), 0.0};
+        double a[2] = {ar[0], ar[1]};
+        bool used = false, moved = false;
+        if (prm.controller && has_ctrl_) {
+          if (ctrl_last && rel_now > rel_prev) {
+            ++ctrl_fallbacks_;  // the last proposal made the KKT residual worse: the rules decide
+          } else {
+            float fx[16], fy[2] = {0.f, 0.f};
+            for (int i = 0; i < 16; ++i) fx[i] = (float)f[i];
+            PDNQP_CK(cudaMemcpyAsync(ctrl_x_, fx, sizeof(fx), cudaMemcpyHostToDevice, s_));
+            if (pdnqp_mlp_forward(ctrl_w_, ctrl_x_, 1, ctrl_y_, nullptr, s_) != 0) {
+              last_err_ = std::string("controller: ") + pdnqp_mlp_last_error();
+              return PDNQP_ERR_CUDA;
+            }
+            PDNQP_CK(cudaMemcpyAsync(fy, ctrl_y_, sizeof(fy), cudaMemcpyDeviceToHost, s_));
+            PDNQP_CK(cudaStreamSynchronize(s_));
+            if (std::isfinite(fy[0]) && std::isfinite(fy[1])) {
+              // The network proposes corrections to the rules' actions.
+              a[0] = ar[0] + fy[0];
+              a[1] = ar[1] + fy[1];
+              used = moved = true;
+              ++ctrl_used_;
+            } else {
+              ++ctrl_fallbacks_;
+            }
+          }
+        }
+        if (prm.ctrl_explore > 0.0) {
+          for (double &v : a) v += prm.ctrl_explore * gauss(rng);
+          moved = true;
+        }
+        if (moved) {
+          rho = prm.rho_in_min + span / (1.0 + std::exp(-a[0]));
+          omega_ *= std::exp(std::min(1.0, std::max(-1.0, a[1])));
+        }
+        trace_.push_back((double)k);
+        trace_.push_back(rel_now);
+        trace_.push_back((double)(accepted_ - acc_before));
+        for (double v : f) trace_.push_back(v);
+        trace_.push_back(ar[0]);
+        trace_.push_back(ar[1]);
+        trace_.push_back(a[0]);
+        trace_.push_back(a[1]);
+        trace_.push_back(used ? 1.0 : 0.0);
+        ctrl_last = used;
+        rel_prev = rel_now;
+        f0_prev = f[0];
+        f1_prev = f[1];
+      }
       dta = std::max(dta * rho, prm.tol_floor * ea);
       dtr = std::max(dtr * rho, prm.tol_floor * er);
       // Eq. center-update / center-tolerance-update.
@@ -1027,6 +1132,8 @@ class Solver : public SolverBase {
     res_.loop_trials = loop_trials_;
     res_.loop_blocks = coop_nb_;
     res_.loop_launches = loop_launches_;
+    res_.ctrl_used = ctrl_used_;
+    res_.ctrl_fallbacks = ctrl_fallbacks_;
     {
       unsigned long long pt[8];
       PDNQP_CK(cudaMemcpy(pt, d_.ptime, sizeof(pt), cudaMemcpyDeviceToHost));
@@ -1128,6 +1235,24 @@ class Solver : public SolverBase {
   long long loop_trials_ = 0;  // trials they ran
   int coop_key_ = -1, coop_nb_ = 0;
   unsigned *hfault_ = nullptr;
+  // learned controller
+  uint16_t *ctrl_w_ = nullptr;
+  float *ctrl_w32_ = nullptr, *ctrl_x_ = nullptr, *ctrl_y_ = nullptr;
+  bool has_ctrl_ = false;
+  std::vector<double> trace_;
+  long long ctrl_used_ = 0, ctrl_fallbacks_ = 0;
+  // Standard normal draw (splitmix64 counter stream, Box-Muller).
+  static double gauss(unsigned long long &s) {
+    auto next = [&s]() {
+      unsigned long long z = (s += 0x9E3779B97F4A7C15ULL);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+      z ^= z >> 31;
+      return ((double)(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    };
+    const double u1 = next(), u2 = next();
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+  }
   float last_replay_ms_ = 0.f;
   int graph_chunk_ = 0;
   bool use_cond_ = true;  // device-driven WHILE/IF graph (else unrolled slots)

@@ -44,10 +44,12 @@ def _sym_offdiag(n: int, rows: np.ndarray, cols: np.ndarray, vals: np.ndarray) -
     """Symmetric matrix with the given (row, col) entries mirrored; diagonal hits dropped."""
     keep = rows != cols
     rows, cols, vals = rows[keep], cols[keep], vals[keep]
-    r = np.concatenate([rows, cols])
-    c = np.concatenate([cols, rows])
-    v = np.concatenate([vals, vals])
-    M = sp.coo_matrix((v, (r, c)), shape=(n, n)).tocsr()
+    # Sum repeated pairs once, in the upper triangle, then mirror the summed
+    # values, so that both triangles hold bit-identical entries.
+    lo, hi = np.minimum(rows, cols), np.maximum(rows, cols)
+    U = sp.coo_matrix((vals, (lo, hi)), shape=(n, n)).tocsr()
+    U.sum_duplicates()
+    M = (U + U.T).tocsr()
     M.sum_duplicates()
     M.sort_indices()
     return M

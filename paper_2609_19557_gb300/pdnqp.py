@@ -25,7 +25,9 @@ SNAP_SCALARS = 8
 EXPORTED = ["pdnqp_create", "pdnqp_create_ex", "pdnqp_destroy", "pdnqp_solve", "pdnqp_get", "pdnqp_set_start",
             "pdnqp_set_param", "pdnqp_get_param", "pdnqp_dims", "pdnqp_last_error", "pdnqp_debug_inner",
             "pdnqp_replay_kernel", "pdnqp_kernel_bytes", "pdnqp_kkt_residuals", "pdnqp_kkt_last_error",
-            "pdnqp_kkt_residuals_noalloc", "pdnqp_replay_last_ms"]
+            "pdnqp_kkt_residuals_noalloc", "pdnqp_replay_last_ms", "pdnqp_mlp_param_count", "pdnqp_mlp_forward",
+            "pdnqp_mlp_wmse", "pdnqp_mlp_backward", "pdnqp_mlp_adam", "pdnqp_mlp_to_bf16", "pdnqp_mlp_last_error",
+            "pdnqp_set_controller", "pdnqp_get_trace"]
 
 
 class pdnqp_csr(C.Structure):
@@ -42,7 +44,7 @@ class pdnqp_residuals(C.Structure):
                 ("inner_seconds", C.c_double), ("setup_seconds", C.c_double),
                 ("loop_seconds", C.c_double), ("loop_trials", C.c_int64), ("loop_blocks", C.c_int64),
                 ("loop_launches", C.c_int64),
-                ("loop_phase_seconds", C.c_double * 6)]
+                ("loop_phase_seconds", C.c_double * 6), ("ctrl_used", C.c_int64), ("ctrl_fallbacks", C.c_int64)]
 
 
 class pdnqp_device_csr(C.Structure):
@@ -98,6 +100,17 @@ def load(path: str | None = None):
     L.pdnqp_kkt_residuals_noalloc.argtypes = [C.POINTER(pdnqp_device_problem), vp, vp, vp, vp]
     L.pdnqp_kkt_last_error.argtypes = []
     L.pdnqp_kkt_last_error.restype = C.c_char_p
+    L.pdnqp_mlp_param_count.argtypes = []
+    L.pdnqp_mlp_forward.argtypes = [vp, vp, ip, vp, vp, vp]
+    L.pdnqp_mlp_wmse.argtypes = [vp, vp, vp, ip, vp, vp, vp]
+    L.pdnqp_mlp_backward.argtypes = [vp, vp, vp, vp, ip, vp, vp, vp]
+    fl = C.c_float
+    L.pdnqp_mlp_adam.argtypes = [vp, vp, vp, vp, vp, ip, fl, fl, fl, fl, vp]
+    L.pdnqp_mlp_to_bf16.argtypes = [vp, vp, ip, vp]
+    L.pdnqp_mlp_last_error.argtypes = []
+    L.pdnqp_mlp_last_error.restype = C.c_char_p
+    L.pdnqp_set_controller.argtypes = [vp, vp, ip]
+    L.pdnqp_get_trace.argtypes = [vp, vp, C.c_int64, vp]
     for name in EXPORTED:
         if not hasattr(L, name):
             raise PdnqpError(f"{p} does not export {name}")
@@ -285,3 +298,70 @@ def pdnqp_kkt_residuals_noalloc(prob: DeviceProblem, x, y, out, stream=None):
                                             out.data_ptr(), C.c_void_p(int(stream)) if stream else None)
     if rc < 0:
         raise PdnqpError(f"pdnqp_kkt_residuals_noalloc error {rc}: {load().pdnqp_kkt_last_error().decode()}")
+
+
+# ---------------------------------------------------------------- controller MLP
+# Thin wrappers over the pdnqp_mlp_* entry points; arguments are torch CUDA
+# tensors (contiguous), the work goes on the current torch stream.
+def _mlp_check(rc):
+    if rc != 0:
+        raise PdnqpError(f"pdnqp_mlp error {rc}: {load().pdnqp_mlp_last_error().decode()}")
+
+
+def _dptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def mlp_param_count() -> int:
+    return int(load().pdnqp_mlp_param_count())
+
+
+def mlp_forward(w_bf16, x, y, cache=None):
+    _mlp_check(load().pdnqp_mlp_forward(_dptr(w_bf16), _dptr(x), int(x.shape[0]), _dptr(y), _dptr(cache), _stream()))
+
+
+def mlp_wmse(y, target, weight, dy, loss=None):
+    _mlp_check(load().pdnqp_mlp_wmse(_dptr(y), _dptr(target), _dptr(weight), int(y.shape[0]), _dptr(dy),
+                                     _dptr(loss), _stream()))
+
+
+def mlp_backward(w_bf16, x, cache, dy, grad, scratch):
+    _mlp_check(load().pdnqp_mlp_backward(_dptr(w_bf16), _dptr(x), _dptr(cache), _dptr(dy), int(x.shape[0]),
+                                         _dptr(grad), _dptr(scratch), _stream()))
+
+
+def mlp_adam(w, w_bf16, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    _mlp_check(load().pdnqp_mlp_adam(_dptr(w), _dptr(w_bf16), _dptr(grad), _dptr(m), _dptr(v), int(step),
+                                     float(lr), float(beta1), float(beta2), float(eps), _stream()))
+
+
+def mlp_to_bf16(w, w_bf16):
+    _mlp_check(load().pdnqp_mlp_to_bf16(_dptr(w), _dptr(w_bf16), int(w.numel()), _stream()))
+
+
+TRACE_COLS = 24
+
+
+def pdnqp_set_controller(h: Handle, weights=None):
+    """Installs (FP32 host array of mlp_param_count() values) or removes (None)
+    the learned controller's weights."""
+    if weights is None:
+        _check(h.ptr, load().pdnqp_set_controller(h.ptr, None, 0))
+        return
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    _check(h.ptr, load().pdnqp_set_controller(h.ptr, w.ctypes.data, int(w.size)))
+
+
+def pdnqp_get_trace(h: Handle) -> np.ndarray:
+    """Per-outer-iteration trace of the last solve, shape (rows, TRACE_COLS)."""
+    n = C.c_int64(0)
+    _check(h.ptr, load().pdnqp_get_trace(h.ptr, None, 0, C.byref(n)))
+    out = np.zeros((n.value, TRACE_COLS))
+    if n.value:
+        _check(h.ptr, load().pdnqp_get_trace(h.ptr, out.ctypes.data, n.value, C.byref(n)))
+    return out
