@@ -55,7 +55,8 @@ class _Params(C.Structure):
                 ("k_chk", C.c_int), ("beta_suff", C.c_double), ("beta_nec", C.c_double),
                 ("beta_art", C.c_double), ("rej_limit", C.c_int), ("kappa_shrink", C.c_double),
                 ("delta_sigma", C.c_double), ("sigma_max", C.c_double), ("tol_floor", C.c_double),
-                ("gamma_override", C.c_double), ("no_scaling", C.c_int), ("verbose", C.c_int)]
+                ("gamma_override", C.c_double), ("no_scaling", C.c_int), ("verbose", C.c_int),
+                ("eps_inf", C.c_double)]
 
 
 class _Result(C.Structure):

@@ -39,6 +39,10 @@
  *     penalties stop growing once the primal part of the termination test holds.
  *   - The center-update tolerances never drop below the final tolerances.
  *   - Outer termination is evaluated on the unscaled problem.
+ *   - Infeasibility tests (Sec. "Infeasibility detection") use the changes of
+ *     lambda and x over one outer iteration on the scaled problem, normalised
+ *     in l_inf, with one tolerance (1e-5): approximate Farkas certificate /
+ *     recession direction with objective decrease (see infeasibility()).
  *
  * Parity pins are in the test-suite: brute-force active-set enumeration,
  * closed forms, invariants (see tests/test_oracle_*.py).  The initial-penalty
@@ -86,6 +90,7 @@ typedef struct {
   double gamma_override; /* > 0: use this gamma instead of the Lanczos choice */
   int no_scaling;        /* 1: skip outer Ruiz and the objective scalar */
   int verbose;           /* 1: one line per outer iteration on stderr */
+  double eps_inf;        /* infeasibility tolerance on l_inf-normalised directions; 0: 1e-5 */
 } or_params;
 
 typedef struct {
@@ -118,6 +123,7 @@ void or_default_params(or_params *p) {
   p->gamma_override = 0.0;
   p->no_scaling = 0;
   p->verbose = 0;
+  p->eps_inf = 0.0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -847,6 +853,67 @@ static void outer_residuals(const sqp_t *S, const double *x, const double *lam, 
   free(ax); free(qx); free(atl);
 }
 
+/* Sec. "Infeasibility detection", on the scaled problem (reading: the
+ * QPALM-style certificate tests with l_inf-normalised directions and one
+ * tolerance eps).
+ * Primal: y = lambda^{k+1} - lambda^k is an approximate Farkas certificate of
+ *   {x in [l_x, u_x] : A x in [l_c, u_c]}: the support function
+ *   sigma_C(y) + sigma_X(-A'y) (sigma_S(v) = sup over S of v's) is below
+ *   -eps ||y||, where every term that would need an infinite bound (the sign
+ *   and stationarity conditions) is at most eps ||y|| in size.
+ * Dual: d = x^{k+1} - x^k is an approximate recession direction (A d in the
+ *   recession cone of [l_c, u_c], d in that of [l_x, u_x], each within
+ *   eps ||d||) along which the objective decreases: d'Qd < -eps ||d||^2, or
+ *   ||Q d|| <= eps ||d|| and c'd < -eps ||d||.
+ * Returns OR_PRIMAL_INFEASIBLE, OR_DUAL_INFEASIBLE or -1. */
+static int infeasibility(const sqp_t *S, const double *dlam, const double *dx, double eps) {
+  const int n = S->n, m = S->m;
+  const double nl = norm_inf(dlam, m), nx = norm_inf(dx, n);
+  if (nl > 0.0) {
+    double *v = dvec((size_t)n);
+    for (int i = 0; i < m; ++i)
+      for (int k = S->A.rp[i]; k < S->A.rp[i + 1]; ++k) v[S->A.ci[k]] -= S->A.v[k] * dlam[i];
+    double sgn = 0.0, sep = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double y = dlam[i];
+      if (y > 0.0) {
+        if (isinf(S->uc[i])) sgn = dmax(sgn, y); else sep += S->uc[i] * y;
+      } else if (y < 0.0) {
+        if (isinf(S->lc[i])) sgn = dmax(sgn, -y); else sep += S->lc[i] * y;
+      }
+    }
+    for (int j = 0; j < n; ++j) {
+      const double w = v[j];
+      if (w > 0.0) {
+        if (isinf(S->ux[j])) sgn = dmax(sgn, w); else sep += S->ux[j] * w;
+      } else if (w < 0.0) {
+        if (isinf(S->lx[j])) sgn = dmax(sgn, -w); else sep += S->lx[j] * w;
+      }
+    }
+    free(v);
+    if (sgn <= eps * nl && sep < -eps * nl) return OR_PRIMAL_INFEASIBLE;
+  }
+  if (nx > 0.0) {
+    double *ad = dvec((size_t)m), *qd = dvec((size_t)n);
+    ocsr_mv(&S->A, dx, ad);
+    ocsr_mv(&S->Q, dx, qd);
+    double rec = 0.0;
+    for (int i = 0; i < m; ++i) {
+      if (!isinf(S->lc[i]) && ad[i] < 0.0) rec = dmax(rec, -ad[i]);
+      if (!isinf(S->uc[i]) && ad[i] > 0.0) rec = dmax(rec, ad[i]);
+    }
+    for (int j = 0; j < n; ++j) {
+      if (!isinf(S->lx[j]) && dx[j] < 0.0) rec = dmax(rec, -dx[j]);
+      if (!isinf(S->ux[j]) && dx[j] > 0.0) rec = dmax(rec, dx[j]);
+    }
+    const double curv = dot(dx, qd, n), lin = dot(S->c, dx, n), qn = norm_inf(qd, n);
+    free(ad);
+    free(qd);
+    if (rec <= eps * nx && (curv < -eps * nx * nx || (qn <= eps * nx && lin < -eps * nx))) return OR_DUAL_INFEASIBLE;
+  }
+  return -1;
+}
+
 static double now_seconds(void) {
   struct timespec ts;
   clock_gettime(CLOCK_MONOTONIC, &ts);
@@ -910,6 +977,8 @@ int or_solve(const or_problem *P, const or_params *prm, double *x_out, double *y
   res->gamma = T.gamma; res->lambda_min = T.lam_min;
   int status = OR_ITER_LIMIT;
   double *ax = dvec((size_t)m), *r = dvec((size_t)m), *xold = dvec((size_t)n);
+  double *lold = dvec((size_t)m), *dl = dvec((size_t)m), *dxv = dvec((size_t)n);
+  const double eps_inf = prm->eps_inf > 0.0 ? prm->eps_inf : 1e-5;
   long long k;
   ores_t sc = {0, 0, 1, 1}, un = {0, 0, 1, 1};
   for (k = 0; k < prm->k_out; ++k) {
@@ -919,6 +988,7 @@ int or_solve(const or_problem *P, const or_params *prm, double *x_out, double *y
     if (ist == IN_NUMERICAL_ERROR) { status = OR_NUMERICAL_ERROR; ++k; break; }
     if (ist == IN_ITER_LIMIT) continue;
     /* Eq. practical-multiplier-update (two-sided reading for I rows). */
+    memcpy(lold, T.lam, sizeof(double) * m);
     ocsr_mv(&S->A, T.x, ax);
     for (int j = 0; j < m; ++j) {
       if (j < S->mE) {
@@ -934,6 +1004,13 @@ int or_solve(const or_problem *P, const or_params *prm, double *x_out, double *y
     outer_residuals(S, T.x, T.lam, &sc, &un);
     if (un.rp <= prm->eps_abs + prm->eps_rel * un.sp && un.rd <= prm->eps_abs + prm->eps_rel * un.sd) {
       status = OR_SOLVED; ++k; break;
+    }
+    /* Sec. "Infeasibility detection". */
+    for (int j = 0; j < m; ++j) dl[j] = T.lam[j] - lold[j];
+    for (int i = 0; i < n; ++i) dxv[i] = T.x[i] - xold[i];
+    {
+      const int inf = infeasibility(S, dl, dxv, eps_inf);
+      if (inf >= 0) { status = inf; ++k; break; }
     }
     /* Eq. penalty-trigger-eq: row-wise increase when the residual did not drop enough,
      * as long as the primal part of Eq. outer-termination is not met yet. */
@@ -984,7 +1061,7 @@ int or_solve(const or_problem *P, const or_params *prm, double *x_out, double *y
     free(qx);
   }
   res->seconds = now_seconds() - t0;
-  free(ax); free(r); free(xold);
+  free(ax); free(r); free(xold); free(lold); free(dl); free(dxv);
   state_free(&T);
   return status;
 }

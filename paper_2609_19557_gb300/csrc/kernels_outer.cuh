@@ -377,6 +377,75 @@ __global__ void __launch_bounds__(kBlock) k_outer_cols(Dev<T> d, Mat<double> Hd,
   block_reduce_store<12>(q, OUT_MAXMASK, d.part + 12 * kMaxBlocks);
 }
 
+// Infeasibility tests (Sec. "Infeasibility detection") on the scaled problem,
+// from the changes over one outer iteration dlam = lambda^{k+1} - lambda^k and
+// dx = x^{k+1} - x^k.  Unnormalised quantities; the host divides by the
+// norms.  Rows (4): 0 largest |dlam_j| that would need an infinite row bound
+// (sign condition), 1 sum of the finite-bound terms of sigma_C(dlam), 2
+// largest departure of (A dx)_j from the recession cone of [l_c, u_c], 3
+// ||dlam||_inf.
+constexpr unsigned INF_R_MAXMASK = 0xDu;
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_inf_rows(Dev<T> d, Mat<double> Ad, const double *lc, const double *uc,
+                                                     const double *lam, const double *lam0, const double *dx) {
+  double q[4] = {0.0, 0.0, 0.0, 0.0};
+  TileIter ti;
+  for (long long tile = ti.first; tile < d.m; tile += ti.step) {
+    const double ad = tile_row_sum<G, double>(Ad.rp, Ad.ci, Ad.val, tile, d.m, [&](int k, double a) { return a * dx[k]; });
+    const long long j = tile + ti.lane;
+    if (j < d.m) {
+      const double y = lam[j] - lam0[j], lo = lc[j], hi = uc[j];
+      if (y > 0.0) {
+        if (isinf(hi)) q[0] = fmax(q[0], y); else q[1] += hi * y;
+      } else if (y < 0.0) {
+        if (isinf(lo)) q[0] = fmax(q[0], -y); else q[1] += lo * y;
+      }
+      if (!isinf(lo) && ad < 0.0) q[2] = fmax(q[2], -ad);
+      if (!isinf(hi) && ad > 0.0) q[2] = fmax(q[2], ad);
+      q[3] = fmax(q[3], fabs(y));
+    }
+  }
+  block_reduce_store<4>(q, INF_R_MAXMASK, d.part);
+}
+
+// Columns (7): 0 largest |v_i|, v = -A' dlam, that would need an infinite
+// variable bound, 1 sum of the finite-bound terms of sigma_X(v), 2 largest
+// departure of dx_i from the recession cone of [l_x, u_x], 3 dx'Q dx, 4 c'dx,
+// 5 ||Q dx||_inf, 6 ||dx||_inf (Q dx = H dx - dx / gamma).
+constexpr unsigned INF_C_MAXMASK = 0x65u;
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_inf_cols(Dev<T> d, Mat<double> Hd, Mat<double> Atd, const double *c,
+                                                     const double *lx, const double *ux, const double *lam,
+                                                     const double *lam0, const double *dx, double ginv) {
+  double q[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  TileIter ti;
+  for (long long tile = ti.first; tile < d.n; tile += ti.step) {
+    const double atl = tile_row_sum<G, double>(Atd.rp, Atd.ci, Atd.val, tile, d.n,
+                                               [&](int k, double a) { return a * (lam[k] - lam0[k]); });
+    const double hd = tile_row_sum<G, double>(Hd.rp, Hd.ci, Hd.val, tile, d.n, [&](int k, double a) { return a * dx[k]; });
+    const long long i = tile + ti.lane;
+    if (i < d.n) {
+      const double v = -atl, di = dx[i], qd = hd - ginv * di, lo = lx[i], hi = ux[i];
+      if (v > 0.0) {
+        if (isinf(hi)) q[0] = fmax(q[0], v); else q[1] += hi * v;
+      } else if (v < 0.0) {
+        if (isinf(lo)) q[0] = fmax(q[0], -v); else q[1] += lo * v;
+      }
+      if (!isinf(lo) && di < 0.0) q[2] = fmax(q[2], -di);
+      if (!isinf(hi) && di > 0.0) q[2] = fmax(q[2], di);
+      q[3] += di * qd;
+      q[4] += c[i] * di;
+      q[5] = fmax(q[5], fabs(qd));
+      q[6] = fmax(q[6], fabs(di));
+    }
+  }
+  block_reduce_store<7>(q, INF_C_MAXMASK, d.part);
+}
+
+__global__ void k_sub(long long n, const double *a, const double *b, double *out) {
+  PDNQP_GRID_STRIDE(i, n) out[i] = a[i] - b[i];
+}
+
 // Eq. penalty-trigger-eq with the growth rule (only when `grow`: the primal
 // part of the termination test still fails).  Stores r as the previous residual.
 __global__ void k_sigma_update(int m, int mE, double *sig, const double *lam, const double *rcur, double *rprev,

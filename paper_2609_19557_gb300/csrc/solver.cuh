@@ -57,6 +57,7 @@ struct Params {
   int controller = 0;          // 1: the learned controller proposes rho_in and the next primal weight
   double ctrl_explore = 0.0;   // std. dev. of Gaussian noise added to the actions (trajectory generation)
   long long ctrl_seed = 0;
+  double eps_inf = 0.0;        // infeasibility tolerance on l_inf-normalised directions (0: 1e-5)
 };
 
 struct Result {

@@ -278,6 +278,9 @@ class Solver : public SolverBase {
     PDNQP_CK(cudaMallocHost(&hfault_, sizeof(unsigned)));
     *hfault_ = 0u;
     PDNQP_TRY(dalloc(&part_, (size_t)kMaxPartials * kMaxBlocks));
+    PDNQP_TRY(dalloc(&xprev_, (size_t)n_));
+    PDNQP_TRY(dalloc(&lamprev_, (size_t)std::max(m_, 1)));
+    PDNQP_TRY(dalloc(&dxv_, (size_t)n_));
     PDNQP_TRY(dalloc(&dred_, 128));
     hred_.resize(128);
     // FP64 matrices.
@@ -981,6 +984,7 @@ class Solver : public SolverBase {
         break;
       }
       const double ts0 = now();
+      PDNQP_CK(cudaMemcpyAsync(xprev_, x64_, sizeof(double) * n_, cudaMemcpyDeviceToDevice, s_));
       PDNQP_TRY(inner_setup(prm, dta, dtr, std::min(prm.k_in, left), -1, 0));
       PDNQP_CK(cudaStreamSynchronize(s_));
       const double ts1 = now();
@@ -1005,6 +1009,7 @@ class Solver : public SolverBase {
       }
       if (S.status == ST_ITER_LIMIT) continue;
       // Multiplier update + outer residuals (Eqs. practical-multiplier-update, outer-residuals).
+      if (m_) PDNQP_CK(cudaMemcpyAsync(lamprev_, lam_, sizeof(double) * m_, cudaMemcpyDeviceToDevice, s_));
       PDNQP_TRY(outer_residuals(1, q));
       const double rps = q[0], sps = std::max(1.0, q[1]), rpu = q[2], spu = std::max(1.0, q[3]), rn = q[4];
       const double rds = q[5], rdu = q[7], sdu = std::max(1.0, q[8]), dxz = q[9];
@@ -1012,6 +1017,15 @@ class Solver : public SolverBase {
         status = PDNQP_SOLVED;
         ++k;
         break;
+      }
+      {
+        int inf = 0;
+        PDNQP_TRY(inf = infeasibility(prm.eps_inf > 0.0 ? prm.eps_inf : 1e-5));
+        if (inf) {
+          status = inf;
+          ++k;
+          break;
+        }
       }
       // Eq. penalty-trigger-eq; penalties grow only while the primal part of
       // Eq. outer-termination fails (scaled or original data).
@@ -1143,6 +1157,38 @@ class Solver : public SolverBase {
     return status;
   }
 
+  // Sec. "Infeasibility detection" on the scaled problem (see k_inf_rows /
+  // k_inf_cols): PDNQP_PRIMAL_INFEASIBLE when lambda^{k+1} - lambda^k is an
+  // approximate Farkas certificate, PDNQP_DUAL_INFEASIBLE when x^{k+1} - x^k
+  // is an approximate recession direction of descent, else 0.
+  int infeasibility(double eps) {
+    const double ginv = 1.0 / gamma_;
+    k_sub<<<grid_n(), kBlock, 0, s_>>>(n_, x64_, xprev_, dxv_);
+    double a[4] = {0.0, 0.0, 0.0, 0.0}, b[7];
+    if (m_) {
+      const int nb = nb_rows();
+      with_G(gA_, [&](auto GG) {
+        k_inf_rows<T, decltype(GG)::value><<<nb, kBlock, 0, s_>>>(d_, Ad_, lcd_, ucd_, lam_, lamprev_, dxv_);
+      });
+      PDNQP_TRY(reduce_to_host(4, nb, INF_R_MAXMASK, a));
+    }
+    {
+      const int nb = nb_cols();
+      with_G(gN_, [&](auto GG) {
+        k_inf_cols<T, decltype(GG)::value><<<nb, kBlock, 0, s_>>>(d_, Hd_, Atd_, c_, lxd_, uxd_, lam_,
+                                                                  m_ ? lamprev_ : lam_, dxv_, ginv);
+      });
+      PDNQP_TRY(reduce_to_host(7, nb, INF_C_MAXMASK, b));
+    }
+    launches_ += m_ ? 3 : 2;
+    const double nl = a[3], nx = b[6];
+    if (nl > 0.0 && std::max(a[0], b[0]) <= eps * nl && a[1] + b[1] < -eps * nl) return PDNQP_PRIMAL_INFEASIBLE;
+    if (nx > 0.0 && std::max(a[2], b[2]) <= eps * nx &&
+        (b[3] < -eps * nx * nx || (b[5] <= eps * nx && b[4] < -eps * nx)))
+      return PDNQP_DUAL_INFEASIBLE;
+    return 0;
+  }
+
   int regamma(double g) {
     // Replace gamma: H = Qbar + g^-1 I (undo the previous shift).
     k_add_diag<<<grid_n(), kBlock, 0, s_>>>(n_, qdiag_, qv_, 1.0 / g - 1.0 / gamma_);
@@ -1236,6 +1282,7 @@ class Solver : public SolverBase {
   int coop_key_ = -1, coop_nb_ = 0;
   unsigned *hfault_ = nullptr;
   // learned controller
+  double *xprev_ = nullptr, *lamprev_ = nullptr, *dxv_ = nullptr;  // infeasibility tests
   uint16_t *ctrl_w_ = nullptr;
   float *ctrl_w32_ = nullptr, *ctrl_x_ = nullptr, *ctrl_y_ = nullptr;
   bool has_ctrl_ = false;

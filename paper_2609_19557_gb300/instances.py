@@ -279,3 +279,44 @@ def make(workload: str, seed: int = 0, **kw) -> dict:
     """Instance by workload name ("small", "mid", "large", "clique", "tiny")."""
     fn = {"small": small_qp, "mid": mid_qp, "large": large_qp, "clique": clique_qp, "tiny": tiny_qp}[workload]
     return fn(seed=seed, **kw)
+
+
+def primal_infeasible_qp(seed: int = 0, n: int = 40, m: int = 20) -> dict:
+    """The small generator with one extra row 1'x_S >= 10 over 5 boxed variables
+    (x in [0, 1]): the constraint set is empty."""
+    inst = small_qp(seed, n=n, m=m)
+    rng = _rng(seed, WORKLOAD_CODES["small"] + 100)
+    cols = np.sort(rng.choice(n, size=5, replace=False))
+    row = sp.csr_matrix((np.ones(5), (np.zeros(5, dtype=int), cols)), shape=(1, n))
+    A = sp.vstack([inst["A"], row]).tocsr()
+    A.sort_indices()
+    l_c = np.append(inst["l_c"], 10.0)
+    u_c = np.append(inst["u_c"], np.inf)
+    return _pack(inst["Q"], inst["c"], A, l_c, u_c, inst["l_x"], inst["u_x"], inst["x0"], workload="primal_inf",
+                 seed=seed, row_cols=cols)
+
+
+def dual_infeasible_qp(seed: int = 0, n: int = 40, m: int = 20) -> dict:
+    """The small generator with variable 0 made free, removed from every row
+    and from Q's off-diagonal part, and Q_00 = -1: the objective is unbounded
+    below along x_0."""
+    inst = small_qp(seed, n=n, m=m)
+    Q = inst["Q"].tolil()
+    Q[0, :] = 0.0
+    Q[:, 0] = 0.0
+    Q[0, 0] = -1.0
+    Q = Q.tocsr()
+    Q.eliminate_zeros()
+    A = inst["A"].tolil()
+    A[:, 0] = 0.0
+    A = A.tocsr()
+    A.eliminate_zeros()
+    l_x, u_x = inst["l_x"].copy(), inst["u_x"].copy()
+    l_x[0], u_x[0] = -np.inf, np.inf
+    x0 = inst["x0"].copy()
+    x0[0] = 0.0
+    l_c, u_c = inst["l_c"].copy(), inst["u_c"].copy()
+    ax = A @ x0  # keep the rows feasible at x0 after removing column 0
+    lo_gap, hi_gap = inst["A"] @ inst["x0"] - inst["l_c"], inst["u_c"] - inst["A"] @ inst["x0"]
+    l_c, u_c = ax - lo_gap, ax + hi_gap
+    return _pack(Q, inst["c"], A, l_c, u_c, l_x, u_x, x0, workload="dual_inf", seed=seed)
