@@ -56,7 +56,7 @@ class _Params(C.Structure):
                 ("beta_art", C.c_double), ("rej_limit", C.c_int), ("kappa_shrink", C.c_double),
                 ("delta_sigma", C.c_double), ("sigma_max", C.c_double), ("tol_floor", C.c_double),
                 ("gamma_override", C.c_double), ("no_scaling", C.c_int), ("verbose", C.c_int),
-                ("eps_inf", C.c_double)]
+                ("eps_inf", C.c_double), ("anderson", C.c_int), ("anderson_mem", C.c_int)]
 
 
 class _Result(C.Structure):
@@ -84,6 +84,7 @@ def lib():
                                                C.c_double, C.c_double, C.c_longlong, C.c_void_p, C.c_void_p,
                                                C.c_void_p]
             L.or_kkt_check.argtypes = [dp(_Problem), C.c_void_p, C.c_void_p, C.c_void_p]
+            L.or_anderson_step.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
             L.or_lanczos_min.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_uint64]
             L.or_lanczos_min.restype = C.c_double
             L.or_tridiag_min_eig.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
@@ -289,3 +290,13 @@ def debug_inner_timed(inst: dict, checkpoints, x0=None, **params):
     got = lib().or_debug_inner_timed(P.ref(), C.byref(prm), len(ck), _ptr(ck), _ptr(out), _ptr(times), _ptr(setup))
     del mE
     return times[:max(got, 0)], float(setup[0])
+
+
+def anderson_step(U, G):
+    """One Type-II Anderson step from stored pairs (rows of U, G, oldest first);
+    returns the extrapolated point or None."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    out = np.zeros(U.shape[1])
+    rc = lib().or_anderson_step(int(U.shape[0]), int(U.shape[1]), _ptr(U), _ptr(G), _ptr(out))
+    return out if rc == 0 else None

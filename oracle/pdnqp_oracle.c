@@ -43,6 +43,11 @@
  *     lambda and x over one outer iteration on the scaled problem, normalised
  *     in l_inf, with one tolerance (1e-5): approximate Farkas certificate /
  *     recession direction with objective decrease (see infeasibility()).
+ *   - Anderson acceleration (Type-II, m_A = 5 stored iterates of (lambda, z))
+ *     runs while the primal termination test holds on two consecutive outer
+ *     iterations; its memory is cleared otherwise, a step that raised the
+ *     relative KKT residual pauses it for m_A iterations, and no step moves
+ *     G(u_k) by more than 10 ||f_k|| (see aa_step()).
  *
  * Parity pins are in the test-suite: brute-force active-set enumeration,
  * closed forms, invariants (see tests/test_oracle_*.py).  The initial-penalty
@@ -91,6 +96,8 @@ typedef struct {
   int no_scaling;        /* 1: skip outer Ruiz and the objective scalar */
   int verbose;           /* 1: one line per outer iteration on stderr */
   double eps_inf;        /* infeasibility tolerance on l_inf-normalised directions; 0: 1e-5 */
+  int anderson;          /* 1: Anderson acceleration of (lambda, z) (Sec. "Anderson acceleration") */
+  int anderson_mem;      /* stored outer iterates m_A */
 } or_params;
 
 typedef struct {
@@ -124,6 +131,8 @@ void or_default_params(or_params *p) {
   p->no_scaling = 0;
   p->verbose = 0;
   p->eps_inf = 0.0;
+  p->anderson = 1;
+  p->anderson_mem = 5;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -914,6 +923,106 @@ static int infeasibility(const sqp_t *S, const double *dlam, const double *dx, d
   return -1;
 }
 
+/* Sec. "Anderson acceleration": classical Type-II Anderson acceleration of the
+ * outer fixed-point map G: u^k = (lambda^k, z^k) -> (lambda^{k+1}, z^{k+1}).
+ * The memory holds the last m_A pairs (u_i, G(u_i)); with residuals
+ * f_i = G(u_i) - u_i and the difference columns dF_a = f_{a+1} - f_a,
+ * dG_a = G(u_{a+1}) - G(u_a) (a over the stored pairs), the coefficients
+ * solve min_g ||f_k - dF g||_2 through the normal equations (dF'dF + mu I) g =
+ * dF' f_k with mu = 1e-12 trace(dF'dF) (plain Gaussian elimination), and the
+ * next point is G(u_k) - dG g. */
+typedef struct {
+  int cap, len, dim;
+  double *u, *g; /* cap x dim each, oldest first */
+} anderson_t;
+
+static void aa_init(anderson_t *A, int cap, int dim) {
+  A->cap = cap < 1 ? 1 : cap;
+  A->len = 0;
+  A->dim = dim;
+  A->u = dvec((size_t)A->cap * dim);
+  A->g = dvec((size_t)A->cap * dim);
+}
+static void aa_free(anderson_t *A) { free(A->u); free(A->g); }
+static void aa_push(anderson_t *A, const double *u, const double *g) {
+  if (A->len == A->cap) {
+    memmove(A->u, A->u + A->dim, sizeof(double) * (size_t)(A->cap - 1) * A->dim);
+    memmove(A->g, A->g + A->dim, sizeof(double) * (size_t)(A->cap - 1) * A->dim);
+    A->len--;
+  }
+  memcpy(A->u + (size_t)A->len * A->dim, u, sizeof(double) * A->dim);
+  memcpy(A->g + (size_t)A->len * A->dim, g, sizeof(double) * A->dim);
+  A->len++;
+}
+/* Writes the extrapolated point to out; returns 0, or -1 without a step. */
+static int aa_step(const anderson_t *A, double *out) {
+  const int L = A->len, D = A->dim, nc = L - 1;
+  if (nc < 1) return -1;
+  double M[16], rhs[4], gam[4];
+  const double *fk_u = A->u + (size_t)(L - 1) * D, *fk_g = A->g + (size_t)(L - 1) * D;
+  for (int a = 0; a < nc; ++a) {
+    rhs[a] = 0.0;
+    for (int b = 0; b < nc; ++b) M[a * nc + b] = 0.0;
+  }
+  for (int i = 0; i < D; ++i) {
+    double df[4];
+    for (int a = 0; a < nc; ++a) {
+      const double f1 = A->g[(size_t)(a + 1) * D + i] - A->u[(size_t)(a + 1) * D + i];
+      const double f0 = A->g[(size_t)a * D + i] - A->u[(size_t)a * D + i];
+      df[a] = f1 - f0;
+    }
+    const double fk = fk_g[i] - fk_u[i];
+    for (int a = 0; a < nc; ++a) {
+      rhs[a] += df[a] * fk;
+      for (int b = 0; b < nc; ++b) M[a * nc + b] += df[a] * df[b];
+    }
+  }
+  double tr = 0.0;
+  for (int a = 0; a < nc; ++a) tr += M[a * nc + a];
+  if (!(tr > 0.0) || !isfinite(tr)) return -1;
+  for (int a = 0; a < nc; ++a) M[a * nc + a] += 1e-12 * tr;
+  /* Gaussian elimination without pivoting (symmetric positive definite). */
+  for (int c = 0; c < nc; ++c) {
+    const double piv = M[c * nc + c];
+    if (!(piv > 0.0)) return -1;
+    for (int r = c + 1; r < nc; ++r) {
+      const double f = M[r * nc + c] / piv;
+      for (int k = c; k < nc; ++k) M[r * nc + k] -= f * M[c * nc + k];
+      rhs[r] -= f * rhs[c];
+    }
+  }
+  for (int c = nc - 1; c >= 0; --c) {
+    double v = rhs[c];
+    for (int k = c + 1; k < nc; ++k) v -= M[c * nc + k] * gam[k];
+    gam[c] = v / M[c * nc + c];
+  }
+  /* Safeguard (reading): no step when the extrapolation moves G(u_k) by more
+   * than 10 ||f_k||_2. */
+  double fn = 0.0, sn = 0.0;
+  for (int i = 0; i < D; ++i) {
+    double v = 0.0;
+    for (int a = 0; a < nc; ++a) v += gam[a] * (A->g[(size_t)(a + 1) * D + i] - A->g[(size_t)a * D + i]);
+    const double fk = fk_g[i] - fk_u[i];
+    fn += fk * fk;
+    sn += v * v;
+    out[i] = fk_g[i] - v;
+  }
+  if (!(sn <= 100.0 * fn)) return -1;
+  return 0;
+}
+
+/* Test entry: one Anderson step from len stored pairs (rows of U and G, oldest
+ * first, len <= 5); returns 0 and writes out (dim), or -1 without a step. */
+int or_anderson_step(int len, int dim, const double *U, const double *G, double *out) {
+  if (len < 1 || len > 5 || dim < 1) return -1;
+  anderson_t A;
+  aa_init(&A, len, dim);
+  for (int i = 0; i < len; ++i) aa_push(&A, U + (size_t)i * dim, G + (size_t)i * dim);
+  const int rc = aa_step(&A, out);
+  aa_free(&A);
+  return rc;
+}
+
 static double now_seconds(void) {
   struct timespec ts;
   clock_gettime(CLOCK_MONOTONIC, &ts);
@@ -979,11 +1088,19 @@ int or_solve(const or_problem *P, const or_params *prm, double *x_out, double *y
   double *ax = dvec((size_t)m), *r = dvec((size_t)m), *xold = dvec((size_t)n);
   double *lold = dvec((size_t)m), *dl = dvec((size_t)m), *dxv = dvec((size_t)n);
   const double eps_inf = prm->eps_inf > 0.0 ? prm->eps_inf : 1e-5;
+  /* Anderson state: u^k = (lambda^k, z^k) at the start of iteration k. */
+  anderson_t AA;
+  aa_init(&AA, prm->anderson_mem, m + n);
+  double *u0 = dvec((size_t)(m + n)), *gu = dvec((size_t)(m + n)), *ue = dvec((size_t)(m + n));
+  int primal_ok_prev = 0, aa_applied = 0, aa_cool = 0;
+  double rel_prev = INFINITY;
   long long k;
   ores_t sc = {0, 0, 1, 1}, un = {0, 0, 1, 1};
   for (k = 0; k < prm->k_out; ++k) {
     if (now_seconds() - t0 > prm->time_limit) { status = OR_TIME_LIMIT; break; }
     memcpy(xold, T.x, sizeof(double) * n);
+    memcpy(u0, T.lam, sizeof(double) * m);
+    memcpy(u0 + m, T.z, sizeof(double) * n);
     int ist = inner_solve(S, prm, T.z, T.lam, T.sig, T.gamma, dta, dtr, T.x, T.yin, &omega, &C, NULL);
     if (ist == IN_NUMERICAL_ERROR) { status = OR_NUMERICAL_ERROR; ++k; break; }
     if (ist == IN_ITER_LIMIT) continue;
@@ -1042,6 +1159,34 @@ int or_solve(const or_problem *P, const or_params *prm, double *x_out, double *y
       eak = dmax(eak * prm->rho_z, prm->eps_abs);
       erk = dmax(erk * prm->rho_z, prm->eps_rel);
     }
+    /* Sec. "Anderson acceleration" (reading: active while the primal part of
+     * the termination test holds on this and the previous outer iteration,
+     * i.e. once the penalties have stopped growing; the memory is cleared
+     * otherwise, and an accelerated step that raised the relative KKT
+     * residual pauses it for m_A iterations). */
+    if (prm->anderson) {
+      const double rel = dmax(un.rp / (1.0 + un.sp), un.rd / (1.0 + un.sd));
+      /* A step that raised the relative KKT residual or lost primal
+       * feasibility switches the acceleration off for the rest of the solve. */
+      if (aa_applied && (rel > rel_prev || !primal_ok)) aa_cool = 1;
+      const int active = primal_ok && primal_ok_prev && aa_cool == 0;
+      if (!active) {
+        AA.len = 0;
+        aa_applied = 0;
+      } else {
+        memcpy(gu, T.lam, sizeof(double) * m);
+        memcpy(gu + m, T.z, sizeof(double) * n);
+        aa_push(&AA, u0, gu);
+        aa_applied = 0;
+        if (aa_step(&AA, ue) == 0) {
+          memcpy(T.lam, ue, sizeof(double) * m);
+          memcpy(T.z, ue + m, sizeof(double) * n);
+          aa_applied = 1;
+        }
+      }
+      rel_prev = rel;
+    }
+    primal_ok_prev = primal_ok;
   }
   /* Unscale and return (Algorithm 3). */
   for (int i = 0; i < n; ++i) x_out[i] = S->Dx[i] * T.x[i];
@@ -1062,6 +1207,8 @@ int or_solve(const or_problem *P, const or_params *prm, double *x_out, double *y
   }
   res->seconds = now_seconds() - t0;
   free(ax); free(r); free(xold); free(lold); free(dl); free(dxv);
+  free(u0); free(gu); free(ue);
+  aa_free(&AA);
   state_free(&T);
   return status;
 }

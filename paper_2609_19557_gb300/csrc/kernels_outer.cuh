@@ -442,6 +442,58 @@ __global__ void __launch_bounds__(kBlock) k_inf_cols(Dev<T> d, Mat<double> Hd, M
   block_reduce_store<7>(q, INF_C_MAXMASK, d.part);
 }
 
+// Anderson acceleration (Sec. "Anderson acceleration"): sums of one Type-II
+// step over the stored pairs (U_a, G_a), a = 0..L-1 oldest first, physical
+// slot (head + a) % cap, D = m + n doubles each.  With f_a = G_a - U_a,
+// dF_a = f_{a+1} - f_a (a < nc = L - 1) and f_k = f_{L-1}: out rows
+// a * nc + b = dF_a'dF_b, nc * nc + a = dF_a'f_k, nc * nc + nc = f_k'f_k.
+template <int NC>
+__global__ void __launch_bounds__(kBlock) k_aa_dots(const double *U, const double *G, int head, int cap, long long D,
+                                                    double *part) {
+  constexpr int NQ = NC * NC + NC + 1;
+  double q[NQ];
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) q[k] = 0.0;
+  PDNQP_GRID_STRIDE(i, D) {
+    double f[NC + 1];
+#pragma unroll
+    for (int a = 0; a <= NC; ++a) {
+      const long long s = (long long)((head + a) % cap) * D;
+      f[a] = G[s + i] - U[s + i];
+    }
+    double df[NC];
+#pragma unroll
+    for (int a = 0; a < NC; ++a) df[a] = f[a + 1] - f[a];
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+#pragma unroll
+      for (int b = 0; b < NC; ++b) q[a * NC + b] += df[a] * df[b];
+      q[NC * NC + a] += df[a] * f[NC];
+    }
+    q[NC * NC + NC] += f[NC] * f[NC];
+  }
+  block_reduce_store<NQ>(q, 0u, part);
+}
+
+// The extrapolated point out = G_{L-1} - sum_a gam_a (G_{a+1} - G_a) and the
+// squared norm of the correction (row 0 of part).
+__global__ void __launch_bounds__(kBlock) k_aa_apply(const double *G, int head, int cap, int nc, long long D,
+                                                     double g0, double g1, double g2, double g3, double *out,
+                                                     double *part) {
+  const double gam[4] = {g0, g1, g2, g3};
+  double sn[1] = {0.0};
+  PDNQP_GRID_STRIDE(i, D) {
+    double v = 0.0;
+    for (int a = 0; a < nc; ++a) {
+      const long long s0 = (long long)((head + a) % cap) * D, s1 = (long long)((head + a + 1) % cap) * D;
+      v += gam[a] * (G[s1 + i] - G[s0 + i]);
+    }
+    out[i] = G[(long long)((head + nc) % cap) * D + i] - v;
+    sn[0] += v * v;
+  }
+  block_reduce_store<1>(sn, 0u, part);
+}
+
 __global__ void k_sub(long long n, const double *a, const double *b, double *out) {
   PDNQP_GRID_STRIDE(i, n) out[i] = a[i] - b[i];
 }

@@ -58,6 +58,8 @@ struct Params {
   double ctrl_explore = 0.0;   // std. dev. of Gaussian noise added to the actions (trajectory generation)
   long long ctrl_seed = 0;
   double eps_inf = 0.0;        // infeasibility tolerance on l_inf-normalised directions (0: 1e-5)
+  int anderson = 1;            // Anderson acceleration of (lambda, z)
+  int anderson_mem = 5;        // stored outer iterates m_A (2..5)
 };
 
 struct Result {

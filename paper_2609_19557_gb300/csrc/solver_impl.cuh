@@ -969,6 +969,17 @@ class Solver : public SolverBase {
     double q[12];
     trace_.clear();
     ctrl_used_ = ctrl_fallbacks_ = 0;
+    // Anderson state of this solve.
+    aa_cap_ = std::max(2, std::min(5, prm.anderson_mem));
+    aa_len_ = aa_head_ = 0;
+    bool aa_applied = false, aa_off = false, aa_pok_prev = false;
+    double aa_rel_prev = INFINITY;
+    if (prm.anderson && !aa_u_) {
+      const size_t D = (size_t)m_ + n_;
+      PDNQP_TRY(dalloc(&aa_u_, kAaRing * D));
+      PDNQP_TRY(dalloc(&aa_g_, kAaRing * D));
+      PDNQP_TRY(dalloc(&aa_out_, D));
+    }
     bool ctrl_last = false;
     double rel_prev = 0.0, f0_prev = 0.0, f1_prev = 0.0;
     unsigned long long rng = (unsigned long long)prm.ctrl_seed * 0x9E3779B97F4A7C15ULL + 0x1234567ULL;
@@ -985,6 +996,7 @@ class Solver : public SolverBase {
       }
       const double ts0 = now();
       PDNQP_CK(cudaMemcpyAsync(xprev_, x64_, sizeof(double) * n_, cudaMemcpyDeviceToDevice, s_));
+      if (prm.anderson) PDNQP_TRY(aa_stage_u());
       PDNQP_TRY(inner_setup(prm, dta, dtr, std::min(prm.k_in, left), -1, 0));
       PDNQP_CK(cudaStreamSynchronize(s_));
       const double ts1 = now();
@@ -1119,6 +1131,26 @@ class Solver : public SolverBase {
         eak = std::max(eak * prm.rho_z, ea);
         erk = std::max(erk * prm.rho_z, er);
       }
+      // Anderson step (active while the primal termination test holds on this
+      // and the previous outer iteration; a step that raised the relative KKT
+      // residual or lost primal feasibility switches it off for the solve).
+      if (prm.anderson) {
+        const double rel = std::max(rpu / (1.0 + spu), rdu / (1.0 + sdu));
+        const int primal_ok = !grow;
+        if (aa_applied && (rel > aa_rel_prev || !primal_ok)) aa_off = true;
+        const bool active = primal_ok && aa_pok_prev && !aa_off;
+        aa_applied = false;
+        if (!active) {
+          aa_len_ = 0;
+        } else {
+          PDNQP_TRY(aa_push_g());
+          int stepped = 0;
+          PDNQP_TRY(stepped = aa_try_step());
+          aa_applied = stepped != 0;
+        }
+        aa_rel_prev = rel;
+        aa_pok_prev = primal_ok;
+      }
       PDNQP_CK(cudaGetLastError());
     }
     // Result in the original coordinates.
@@ -1155,6 +1187,85 @@ class Solver : public SolverBase {
     }
     solved_once_ = true;
     return status;
+  }
+
+  // Anderson acceleration (Sec. "Anderson acceleration"), Type-II on u =
+  // (lambda, z) with the last anderson_mem pairs (u_k, G(u_k)) in a ring on
+  // the device: the sums go through k_aa_dots, the small normal equations
+  // (dF'dF + 1e-12 tr I) g = dF'f_k are solved here by Gaussian elimination,
+  // and the step is skipped when it would move G(u_k) by more than
+  // 10 ||f_k||_2.  Returns 1 when (lambda, z) were replaced.
+  int aa_try_step() {
+    const int L = aa_len_, nc = L - 1;
+    if (nc < 1) return 0;
+    const long long D = (long long)m_ + n_;
+    const int nb = grid_for(D, kBlock);
+    const int nq = nc * nc + nc + 1;
+    switch (nc) {
+      case 1: k_aa_dots<1><<<nb, kBlock, 0, s_>>>(aa_u_, aa_g_, aa_head_, kAaRing, D, part_); break;
+      case 2: k_aa_dots<2><<<nb, kBlock, 0, s_>>>(aa_u_, aa_g_, aa_head_, kAaRing, D, part_); break;
+      case 3: k_aa_dots<3><<<nb, kBlock, 0, s_>>>(aa_u_, aa_g_, aa_head_, kAaRing, D, part_); break;
+      default: k_aa_dots<4><<<nb, kBlock, 0, s_>>>(aa_u_, aa_g_, aa_head_, kAaRing, D, part_); break;
+    }
+    double q[21];
+    PDNQP_TRY(reduce_to_host(nq, nb, 0u, q));
+    double M[16], r[4], g[4] = {0.0, 0.0, 0.0, 0.0};
+    double tr = 0.0;
+    for (int a = 0; a < nc; ++a) {
+      for (int b = 0; b < nc; ++b) M[a * nc + b] = q[a * nc + b];
+      r[a] = q[nc * nc + a];
+      tr += M[a * nc + a];
+    }
+    const double fn = q[nc * nc + nc];
+    if (!(tr > 0.0) || !std::isfinite(tr)) return 0;
+    for (int a = 0; a < nc; ++a) M[a * nc + a] += 1e-12 * tr;
+    for (int c = 0; c < nc; ++c) {
+      const double piv = M[c * nc + c];
+      if (!(piv > 0.0)) return 0;
+      for (int rr = c + 1; rr < nc; ++rr) {
+        const double f = M[rr * nc + c] / piv;
+        for (int k = c; k < nc; ++k) M[rr * nc + k] -= f * M[c * nc + k];
+        r[rr] -= f * r[c];
+      }
+    }
+    for (int c = nc - 1; c >= 0; --c) {
+      double v = r[c];
+      for (int k = c + 1; k < nc; ++k) v -= M[c * nc + k] * g[k];
+      g[c] = v / M[c * nc + c];
+    }
+    k_aa_apply<<<nb, kBlock, 0, s_>>>(aa_g_, aa_head_, kAaRing, nc, D, g[0], g[1], g[2], g[3], aa_out_, part_);
+    double sn = 0.0;
+    PDNQP_TRY(reduce_to_host(1, nb, 0u, &sn));
+    launches_ += 2;
+    if (!(sn <= 100.0 * fn)) return 0;
+    if (m_) PDNQP_CK(cudaMemcpyAsync(lam_, aa_out_, sizeof(double) * m_, cudaMemcpyDeviceToDevice, s_));
+    PDNQP_CK(cudaMemcpyAsync(z_, aa_out_ + m_, sizeof(double) * n_, cudaMemcpyDeviceToDevice, s_));
+    return 1;
+  }
+  // Ring of kAaRing = 6 slots (logical pair a at (head + a) % 6, at most
+  // aa_cap_ <= 5 pairs), so the slot after the last pair is always free: it
+  // receives u, the point this outer iteration starts from.
+  int aa_stage_u() {
+    const long long D = (long long)m_ + n_;
+    const int slot = (aa_head_ + aa_len_) % kAaRing;
+    double *u = aa_u_ + (size_t)slot * D;
+    if (m_) PDNQP_CK(cudaMemcpyAsync(u, lam_, sizeof(double) * m_, cudaMemcpyDeviceToDevice, s_));
+    PDNQP_CK(cudaMemcpyAsync(u + m_, z_, sizeof(double) * n_, cudaMemcpyDeviceToDevice, s_));
+    return 0;
+  }
+  // Appends G(u) = (lambda, z) to the staged slot (dropping the oldest pair when full).
+  int aa_push_g() {
+    const long long D = (long long)m_ + n_;
+    const int slot = (aa_head_ + aa_len_) % kAaRing;
+    double *g = aa_g_ + (size_t)slot * D;
+    if (m_) PDNQP_CK(cudaMemcpyAsync(g, lam_, sizeof(double) * m_, cudaMemcpyDeviceToDevice, s_));
+    PDNQP_CK(cudaMemcpyAsync(g + m_, z_, sizeof(double) * n_, cudaMemcpyDeviceToDevice, s_));
+    if (aa_len_ == aa_cap_) {
+      aa_head_ = (aa_head_ + 1) % kAaRing;
+    } else {
+      ++aa_len_;
+    }
+    return 0;
   }
 
   // Sec. "Infeasibility detection" on the scaled problem (see k_inf_rows /
@@ -1283,6 +1394,9 @@ class Solver : public SolverBase {
   unsigned *hfault_ = nullptr;
   // learned controller
   double *xprev_ = nullptr, *lamprev_ = nullptr, *dxv_ = nullptr;  // infeasibility tests
+  double *aa_u_ = nullptr, *aa_g_ = nullptr, *aa_out_ = nullptr;    // Anderson ring and step
+  static constexpr int kAaRing = 6;
+  int aa_cap_ = 5, aa_len_ = 0, aa_head_ = 0;
   uint16_t *ctrl_w_ = nullptr;
   float *ctrl_w32_ = nullptr, *ctrl_x_ = nullptr, *ctrl_y_ = nullptr;
   bool has_ctrl_ = false;
