@@ -1,0 +1,61 @@
+"""Parity at the benchmark's full size (n = 1e6, m = 5e5) in the launch
+configuration bench.py times (persistent trial loop, 3 blocks/SM in FP32):
+the first inner iterations against the oracle's own run of the same
+iterations (FP64 within 1e-10, FP32-bulk within 1e-4 relative), and the
+solver's reported residuals against the oracle's external KKT test."""
+import numpy as np
+import pytest
+
+from paper_2609_19557_gb300 import instances as I
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+CK = [1, 2, 3, 5]
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2609_19557_gb300 import build as B
+    from paper_2609_19557_gb300 import pdnqp
+    B.build()
+    pdnqp.load()
+    return pdnqp
+
+
+@pytest.fixture(scope="module")
+def large():
+    return I.large_qp(0)
+
+
+@pytest.fixture(scope="module")
+def ref(oracle, large):
+    return oracle.debug_inner(large, CK)
+
+
+def rel_err(a, b):
+    return np.abs(a - b).max(initial=0.0) / max(np.abs(b).max(initial=0.0), 1e-300)
+
+
+@pytest.mark.parametrize("precision,tol", [(64, 1e-10), (32, 1e-4)])
+def test_full_size_first_iterations(P, large, ref, precision, tol):
+    snaps, info = ref
+    h = P.create_from_instance(large, precision=precision)
+    gpu = P.pdnqp_debug_inner(h, CK)
+    assert abs(P.pdnqp_get_param(h, "gamma") - info["gamma"]) <= 1e-10 * info["gamma"]
+    h.close()
+    for s, r, c in zip(gpu, snaps, CK):
+        assert s["t_total"] == r["t_total"] == c
+        e = max(rel_err(s[k], r[k]) for k in ("w", "y", "wbar", "ybar"))
+        assert e <= tol, (precision, c, e)
+
+
+def test_full_size_residuals_match_external_test(P, oracle, large):
+    h = P.create_from_instance(large, precision=32)
+    P.pdnqp_set_param(h, "iter_budget", 300)
+    P.pdnqp_solve(h, 1e-4, 1e-4)
+    x, y, r = P.pdnqp_get(h)
+    h.close()
+    rp, rd, sp, sd = oracle.kkt_check(large, x, y)
+    assert np.allclose([r["r_p"], r["r_d"], r["s_p"], r["s_d"]], [rp, rd, sp, sd], rtol=1e-9, atol=1e-12)
