@@ -145,6 +145,7 @@ template <bool COND>
 __device__ void check_final_body(DevState *stg, const double *part, int nb_r, int nb_c,
                                  cudaGraphConditionalHandle hw);
 __device__ void inner_begin_body(DevState *st, const double *part, int nb_r, int nb_c);
+__device__ __forceinline__ void decide_logic(DevState *st, const double (&a)[4], const double (&b)[4]);
 
 // ===========================================================================
 // Trial step (Eq. pdqp-trial) and acceptance test (Eq. adaptive-condition).
@@ -459,11 +460,12 @@ __device__ __forceinline__ void stream_issue(StreamCtl &ctl, unsigned char *buf,
   fence_proxy_async_smem();
   mbar_arrive_expect_tx(&ctl.bar[st], fits ? total : 0u);
   if (fits) {
+    const unsigned long long pol = l2_evict_first_policy();
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
       if (c[m] > 0) {
-        bulk_g2s(dst + o[m], M[m].ci + a[m], (unsigned)c[m] * 4u, &ctl.bar[st]);
-        bulk_g2s(dst + o[m] + 4 * c[m], M[m].val + a[m], (unsigned)c[m] * (unsigned)sizeof(T), &ctl.bar[st]);
+        bulk_g2s_hint(dst + o[m], M[m].ci + a[m], (unsigned)c[m] * 4u, &ctl.bar[st], pol);
+        bulk_g2s_hint(dst + o[m] + 4 * c[m], M[m].val + a[m], (unsigned)c[m] * (unsigned)sizeof(T), &ctl.bar[st], pol);
       }
     }
   }
@@ -801,6 +803,39 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 2) k_trials(Dev<T
 // rejection both step vectors shrink through kappa.  Sets the device-loop
 // handles: hw (continue while running and the launch has trials left) and hc
 // (a periodic check follows).
+// The scalar part of the acceptance decision (one thread), from the row (a)
+// and column (b) sums of the trial.
+__device__ __forceinline__ void decide_logic(DevState *st, const double (&a)[4], const double (&b)[4]) {
+  // Commit the averages materialised by this trial's primal / row passes.
+  st->acur ^= st->accepted;
+  st->accepted = 0;
+  st->restart_flag = 0;
+  st->check_due = 0;
+  st->trials += 1;
+  const double om = st->omega, ka = st->kappa;
+  const double lhs = (om / ka) * (a[0] + b[0]) + (a[1] + b[1]) / (ka * om);
+  const double rh = a[2] + b[2], rb = a[3] + b[3];
+  if (!isfinite(lhs) || !isfinite(rh) || !isfinite(rb)) {
+    st->status = ST_NUMERICAL_ERROR;
+  } else if (0.5 * lhs >= 0.5 * rh + rb) {
+    st->alpha_acc = 2.0 / ((double)st->t + 2.0);
+    st->cur ^= 1;
+    st->accepted = 1;
+    st->t += 1;
+    st->t_total += 1;
+    st->accepted_all += 1;
+    st->rej = 0;
+    const bool due = (st->k_chk > 0 && st->t_total % st->k_chk == 0) || st->t_total == st->k_in;
+    st->check_due = due ? 1 : 0;
+    if (!due && st->t_total == st->pause_at) st->status = ST_PAUSED;
+  } else {
+    st->kappa *= st->shrink;
+    st->rej += 1;
+    if (st->rej >= st->rej_limit) st->status = ST_NUMERICAL_ERROR;
+  }
+  st->slot_left -= 1;
+}
+
 template <bool COND>
 __device__ void decide_body(DevState *stg, const double *part, int nb_r, int nb_c, cudaGraphConditionalHandle hw,
                             cudaGraphConditionalHandle hc) {
@@ -820,39 +855,11 @@ __device__ void decide_body(DevState *stg, const double *part, int nb_r, int nb_
     final_reduce<4>(part + P_TR_C * kMaxBlocks, nb_c, 0u, b);
   }
   if (threadIdx.x == 0) {
-    DevState *st = &S;
-    // Commit the averages materialised by this slot's primal / row kernels.
-    st->acur ^= st->accepted;
-    st->accepted = 0;
-    st->restart_flag = 0;
-    st->check_due = 0;
-    st->trials += 1;
-    const double om = st->omega, ka = st->kappa;
-    const double lhs = (om / ka) * (a[0] + b[0]) + (a[1] + b[1]) / (ka * om);
-    const double rh = a[2] + b[2], rb = a[3] + b[3];
-    if (!isfinite(lhs) || !isfinite(rh) || !isfinite(rb)) {
-      st->status = ST_NUMERICAL_ERROR;
-    } else if (0.5 * lhs >= 0.5 * rh + rb) {
-      st->alpha_acc = 2.0 / ((double)st->t + 2.0);
-      st->cur ^= 1;
-      st->accepted = 1;
-      st->t += 1;
-      st->t_total += 1;
-      st->accepted_all += 1;
-      st->rej = 0;
-      const bool due = (st->k_chk > 0 && st->t_total % st->k_chk == 0) || st->t_total == st->k_in;
-      st->check_due = due ? 1 : 0;
-      if (!due && st->t_total == st->pause_at) st->status = ST_PAUSED;
-    } else {
-      st->kappa *= st->shrink;
-      st->rej += 1;
-      if (st->rej >= st->rej_limit) st->status = ST_NUMERICAL_ERROR;
-    }
-    st->slot_left -= 1;
+    decide_logic(&S, a, b);
     if (COND) {
-      const bool run = st->status == ST_RUNNING;
-      if (hw) cudaGraphSetConditional(hw, (run && st->slot_left > 0) ? 1u : 0u);
-      if (hc) cudaGraphSetConditional(hc, (run && st->check_due) ? 1u : 0u);
+      const bool run = S.status == ST_RUNNING;
+      if (hw) cudaGraphSetConditional(hw, (run && S.slot_left > 0) ? 1u : 0u);
+      if (hc) cudaGraphSetConditional(hc, (run && S.check_due) ? 1u : 0u);
     }
   }
   state_store(stg, S);
