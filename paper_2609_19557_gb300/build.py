@@ -54,7 +54,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
         outs = list(ex.map(one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([cc, "-shared", "-o", tmp, *[o for o, _ in outs]], capture_output=True, text=True)
+    r = subprocess.run([cc, "-shared", "-o", tmp, *[o for o, _ in outs], "-lpthread"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)

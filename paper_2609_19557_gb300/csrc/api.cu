@@ -5,11 +5,15 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/pdnqp.h"
@@ -30,6 +34,7 @@ struct pdnqp {
   int device = 0;
   int precision = PDNQP_FP64;
   int64_t nnzq = 0;
+  double t_prepare = 0.0, t_setup = 0.0;  // wall time of pdnqp_create's host preparation and device setup
 };
 
 static thread_local std::string g_err;
@@ -45,6 +50,49 @@ static double clean_bound(double v) {
   if (v <= -1e20) return -INFINITY;
   return v;
 }
+
+// ---------------------------------------------------------------------------
+// Host preparation, parallel over row ranges (std::thread; the results do
+// not depend on the number of threads).
+// ---------------------------------------------------------------------------
+static int host_threads() {
+  const unsigned hc = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(hc == 0 ? 1u : hc, 32u));
+}
+
+// Runs f(lo, hi, t) on [0, n) split into contiguous ranges, one per thread.
+template <typename F>
+static void parallel_for(long long n, F f) {
+  const int T = (int)std::min<long long>(host_threads(), std::max<long long>(1, n / 4096));
+  if (T <= 1) {
+    f(0LL, n, 0);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(T);
+  for (int t = 0; t < T; ++t) {
+    const long long lo = n * t / T, hi = n * (t + 1) / T;
+    th.emplace_back([=, &f] { f(lo, hi, t); });
+  }
+  for (auto &x : th) x.join();
+}
+
+// First error found by any thread (the one on the lowest row wins, so the
+// message does not depend on the thread count).
+struct ErrSlot {
+  std::mutex mu;
+  long long row = -1;
+  int code = 0;
+  std::string msg;
+  void set(long long r, int c, std::string m) {
+    std::lock_guard<std::mutex> g(mu);
+    if (row < 0 || r < row) {
+      row = r;
+      code = c;
+      msg = std::move(m);
+    }
+  }
+};
 
 // Validates a host CSR matrix; returns its rows with columns sorted.
 static int read_csr(const pdnqp_csr *M, int rows, int cols, const char *name, std::vector<int> &rp,
@@ -65,61 +113,132 @@ static int read_csr(const pdnqp_csr *M, int rows, int cols, const char *name, st
     msg = std::string(name) + ": row_ptr[0] must be 0 and row_ptr[n_rows] == nnz";
     return PDNQP_ERR_ARG;
   }
-  rp.assign(rows + 1, 0);
-  ci.resize(M->nnz);
-  v.resize(M->nnz);
-  std::vector<std::pair<int, double>> tmp;
-  for (int i = 0; i < rows; ++i) {
-    const int b = M->row_ptr[i], e = M->row_ptr[i + 1];
-    if (e < b) {
+  for (int i = 0; i < rows; ++i)
+    if (M->row_ptr[i + 1] < M->row_ptr[i]) {
       msg = std::string(name) + ": row_ptr not monotone";
       return PDNQP_ERR_ARG;
     }
-    tmp.clear();
-    for (int k = b; k < e; ++k) {
-      const int c = M->col_idx[k];
-      if (c < 0 || c >= cols) {
-        msg = std::string(name) + ": column index out of range";
-        return PDNQP_ERR_ARG;
+  rp.assign(M->row_ptr, M->row_ptr + rows + 1);
+  ci.resize(M->nnz);
+  v.resize(M->nnz);
+  ErrSlot err;
+  parallel_for(rows, [&](long long lo, long long hi, int) {
+    std::vector<std::pair<int, double>> tmp;
+    for (long long i = lo; i < hi; ++i) {
+      const int b = M->row_ptr[i], e = M->row_ptr[i + 1];
+      bool sorted = true;
+      for (int k = b; k < e; ++k) {
+        const int c = M->col_idx[k];
+        if (c < 0 || c >= cols) {
+          err.set(i, PDNQP_ERR_ARG, std::string(name) + ": column index out of range");
+          return;
+        }
+        if (!std::isfinite(M->val[k])) {
+          err.set(i, PDNQP_ERR_BOUNDS, std::string(name) + ": non-finite value");
+          return;
+        }
+        if (k > b && c <= M->col_idx[k - 1]) sorted = false;
       }
-      if (!std::isfinite(M->val[k])) {
-        msg = std::string(name) + ": non-finite value";
-        return PDNQP_ERR_BOUNDS;
+      if (sorted) {  // strictly increasing: no sort, no duplicates
+        std::copy(M->col_idx + b, M->col_idx + e, ci.begin() + b);
+        std::copy(M->val + b, M->val + e, v.begin() + b);
+        continue;
       }
-      tmp.push_back({c, M->val[k]});
+      tmp.clear();
+      for (int k = b; k < e; ++k) tmp.push_back({M->col_idx[k], M->val[k]});
+      std::sort(tmp.begin(), tmp.end(), [](const std::pair<int, double> &x, const std::pair<int, double> &y) {
+        return x.first < y.first;
+      });
+      for (size_t k = 1; k < tmp.size(); ++k)
+        if (tmp[k].first == tmp[k - 1].first) {
+          err.set(i, PDNQP_ERR_ARG, std::string(name) + ": duplicate entry");
+          return;
+        }
+      for (size_t k = 0; k < tmp.size(); ++k) {
+        ci[b + k] = tmp[k].first;
+        v[b + k] = tmp[k].second;
+      }
     }
-    std::sort(tmp.begin(), tmp.end(), [](const std::pair<int, double> &a, const std::pair<int, double> &b2) {
-      return a.first < b2.first;
-    });
-    for (size_t k = 1; k < tmp.size(); ++k)
-      if (tmp[k].first == tmp[k - 1].first) {
-        msg = std::string(name) + ": duplicate entry";
-        return PDNQP_ERR_ARG;
-      }
-    for (size_t k = 0; k < tmp.size(); ++k) {
-      ci[b + k] = tmp[k].first;
-      v[b + k] = tmp[k].second;
-    }
-    rp[i + 1] = e;
+  });
+  if (err.code) {
+    msg = err.msg;
+    return err.code;
   }
   return 0;
 }
 
+// Symmetry of a square CSR with sorted rows: every entry (i, j, v) has the
+// entry (j, i, v) (binary search in row j).
+static bool symmetric(int n, const std::vector<int> &rp, const std::vector<int> &ci, const std::vector<double> &v) {
+  std::atomic<bool> ok(true);
+  parallel_for(n, [&](long long lo, long long hi, int) {
+    for (long long i = lo; i < hi && ok.load(std::memory_order_relaxed); ++i)
+      for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        const int j = ci[k];
+        const int *b = ci.data() + rp[j], *e = ci.data() + rp[j + 1];
+        const int *f = std::lower_bound(b, e, (int)i);
+        if (f == e || *f != (int)i || v[f - ci.data()] != v[k]) {
+          ok = false;
+          return;
+        }
+      }
+  });
+  return ok;
+}
+
+// Transpose of a CSR (rows sorted by column in the result): per-thread
+// column counts over contiguous row ranges, offsets thread by thread within
+// each column, then each thread scatters its rows in order.
 static void transpose(int rows, int cols, const std::vector<int> &rp, const std::vector<int> &ci,
                       const std::vector<double> &v, std::vector<int> &trp, std::vector<int> &tci,
                       std::vector<double> &tv) {
   trp.assign(cols + 1, 0);
   tci.resize(ci.size());
   tv.resize(v.size());
-  for (int c : ci) trp[c + 1]++;
-  for (int i = 0; i < cols; ++i) trp[i + 1] += trp[i];
-  std::vector<int> pos(trp.begin(), trp.end() - 1);
-  for (int i = 0; i < rows; ++i)
-    for (int k = rp[i]; k < rp[i + 1]; ++k) {
-      const int d = pos[ci[k]]++;
-      tci[d] = i;
-      tv[d] = v[k];
+  const int T = (int)std::min<long long>(host_threads(), std::max<long long>(1, rows / 4096));
+  std::vector<std::vector<int>> cnt(T, std::vector<int>(cols, 0));
+  auto range = [&](int t, long long &lo, long long &hi) {
+    lo = (long long)rows * t / T;
+    hi = (long long)rows * (t + 1) / T;
+  };
+  {
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; ++t)
+      th.emplace_back([&, t] {
+        long long lo, hi;
+        range(t, lo, hi);
+        for (long long i = lo; i < hi; ++i)
+          for (int k = rp[i]; k < rp[i + 1]; ++k) cnt[t][ci[k]]++;
+      });
+    for (auto &x : th) x.join();
+  }
+  // offsets: column c starts at trp[c]; within it, thread t's entries follow thread t-1's
+  long long acc = 0;
+  for (int c = 0; c < cols; ++c) {
+    trp[c] = (int)acc;
+    for (int t = 0; t < T; ++t) {
+      const int k = cnt[t][c];
+      cnt[t][c] = (int)acc;
+      acc += k;
     }
+  }
+  trp[cols] = (int)acc;
+  {
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; ++t)
+      th.emplace_back([&, t] {
+        long long lo, hi;
+        range(t, lo, hi);
+        std::vector<int> &pos = cnt[t];
+        for (long long i = lo; i < hi; ++i)
+          for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            const int d = pos[ci[k]]++;
+            tci[d] = (int)i;
+            tv[d] = v[k];
+          }
+      });
+    for (auto &x : th) x.join();
+  }
 }
 
 static int prepare(const pdnqp_csr *Q, const double *c, const pdnqp_csr *A, const double *l_c, const double *u_c,
@@ -144,44 +263,51 @@ static int prepare(const pdnqp_csr *Q, const double *c, const pdnqp_csr *A, cons
   std::vector<double> qv;
   int rc = read_csr(Q, n, n, "Q", qrp, qci, qv, msg);
   if (rc) return rc;
-  {  // symmetry: the transpose of the sorted CSR must be identical
-    std::vector<int> trp, tci;
-    std::vector<double> tv;
-    transpose(n, n, qrp, qci, qv, trp, tci, tv);
-    if (trp != qrp || tci != qci || tv != qv) {
-      msg = "Q is not symmetric with both triangles stored";
-      return PDNQP_ERR_NOT_SYMMETRIC;
-    }
+  if (!symmetric(n, qrp, qci, qv)) {
+    msg = "Q is not symmetric with both triangles stored";
+    return PDNQP_ERR_NOT_SYMMETRIC;
   }
-  // Q with an explicit diagonal entry in every row.
+  // Q with an explicit diagonal entry in every row: new row lengths, offsets,
+  // then a parallel fill.
   P.q_rp.assign(n + 1, 0);
   P.q_diag.assign(n, 0);
-  P.q_ci.clear();
-  P.q_v.clear();
-  P.q_ci.reserve(qci.size() + n);
-  P.q_v.reserve(qci.size() + n);
-  for (int i = 0; i < n; ++i) {
-    bool done = false;
-    for (int k = qrp[i]; k < qrp[i + 1]; ++k) {
-      if (!done && qci[k] >= i) {
-        if (qci[k] != i) {
-          P.q_diag[i] = (int)P.q_ci.size();
-          P.q_ci.push_back(i);
-          P.q_v.push_back(0.0);
-        } else {
-          P.q_diag[i] = (int)P.q_ci.size();
-        }
-        done = true;
+  {
+    std::vector<char> has(n, 0);
+    parallel_for(n, [&](long long lo, long long hi, int) {
+      for (long long i = lo; i < hi; ++i) {
+        const int *b = qci.data() + qrp[i], *e = qci.data() + qrp[i + 1];
+        const int *f = std::lower_bound(b, e, (int)i);
+        has[i] = (f != e && *f == (int)i) ? 1 : 0;
       }
-      P.q_ci.push_back(qci[k]);
-      P.q_v.push_back(qv[k]);
-    }
-    if (!done) {
-      P.q_diag[i] = (int)P.q_ci.size();
-      P.q_ci.push_back(i);
-      P.q_v.push_back(0.0);
-    }
-    P.q_rp[i + 1] = (int)P.q_ci.size();
+    });
+    for (int i = 0; i < n; ++i) P.q_rp[i + 1] = P.q_rp[i] + (qrp[i + 1] - qrp[i]) + (has[i] ? 0 : 1);
+    P.q_ci.resize(P.q_rp[n]);
+    P.q_v.resize(P.q_rp[n]);
+    parallel_for(n, [&](long long lo, long long hi, int) {
+      for (long long i = lo; i < hi; ++i) {
+        int o = P.q_rp[i];
+        bool done = false;
+        for (int k = qrp[i]; k < qrp[i + 1]; ++k) {
+          if (!done && qci[k] >= (int)i) {
+            P.q_diag[i] = o;
+            if (qci[k] != (int)i) {
+              P.q_ci[o] = (int)i;
+              P.q_v[o] = 0.0;
+              ++o;
+            }
+            done = true;
+          }
+          P.q_ci[o] = qci[k];
+          P.q_v[o] = qv[k];
+          ++o;
+        }
+        if (!done) {
+          P.q_diag[i] = o;
+          P.q_ci[o] = (int)i;
+          P.q_v[o] = 0.0;
+        }
+      }
+    });
   }
   P.c.assign(c, c + n);
   P.lx.resize(n);
@@ -222,20 +348,23 @@ static int prepare(const pdnqp_csr *Q, const double *c, const pdnqp_csr *A, cons
   for (int j = 0; j < m; ++j)
     if (lo[j] != hi[j]) P.perm.push_back(j);
   P.a_rp.assign(m + 1, 0);
-  P.a_ci.clear();
-  P.a_v.clear();
   P.lc.resize(m);
   P.uc.resize(m);
   for (int r = 0; r < m; ++r) {
     const int j = P.perm[r];
-    for (int k = arp[j]; k < arp[j + 1]; ++k) {
-      P.a_ci.push_back(aci[k]);
-      P.a_v.push_back(av[k]);
-    }
-    P.a_rp[r + 1] = (int)P.a_ci.size();
+    P.a_rp[r + 1] = P.a_rp[r] + (arp[j + 1] - arp[j]);
     P.lc[r] = lo[j];
     P.uc[r] = hi[j];
   }
+  P.a_ci.resize(P.a_rp[m]);
+  P.a_v.resize(P.a_rp[m]);
+  parallel_for(m, [&](long long r0, long long r1, int) {
+    for (long long r = r0; r < r1; ++r) {
+      const int j = P.perm[r];
+      std::copy(aci.begin() + arp[j], aci.begin() + arp[j + 1], P.a_ci.begin() + P.a_rp[r]);
+      std::copy(av.begin() + arp[j], av.begin() + arp[j + 1], P.a_v.begin() + P.a_rp[r]);
+    }
+  });
   transpose(m, n, P.a_rp, P.a_ci, P.a_v, P.at_rp, P.at_ci, P.at_v);
   return 0;
 }
@@ -261,8 +390,10 @@ int pdnqp_create_ex(pdnqp_t **out, const pdnqp_csr *Q, const double *c, const pd
   }
   HostProblem P;
   std::string msg;
+  const auto t0 = std::chrono::steady_clock::now();
   int rc = prepare(Q, c, A, l_c, u_c, l_x, u_x, P, msg);
   if (rc) return fail(nullptr, rc, msg);
+  const auto t1 = std::chrono::steady_clock::now();
   pdnqp_t *h = new (std::nothrow) pdnqp_t();
   if (!h) return fail(nullptr, PDNQP_ERR_OOM, "host allocation failed");
   h->n = P.n;
@@ -281,6 +412,9 @@ int pdnqp_create_ex(pdnqp_t **out, const pdnqp_csr *Q, const double *c, const pd
     delete h;
     return rc;
   }
+  const auto t2 = std::chrono::steady_clock::now();
+  h->t_prepare = std::chrono::duration<double>(t1 - t0).count();
+  h->t_setup = std::chrono::duration<double>(t2 - t1).count();
   *out = h;
   return 0;
 }
@@ -405,6 +539,14 @@ int pdnqp_get_param(const pdnqp_t *h, const char *name, double *value) {
   }
   if (s == "precision") {
     *value = h->precision;
+    return 0;
+  }
+  if (s == "create_prepare_seconds") {
+    *value = h->t_prepare;
+    return 0;
+  }
+  if (s == "create_setup_seconds") {
+    *value = h->t_setup;
     return 0;
   }
 #define X(nm, kind, lo, hi) \
