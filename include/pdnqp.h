@@ -167,7 +167,15 @@ PDNQP_API int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0);
  * loop_blocks_per_sm (blocks per SM of that launch; 0 = as many as fit),
  * cond_graph (with persistent = 0; 1: inner loop as a device-driven CUDA
  * graph with conditional WHILE/IF nodes; 0: unrolled graph of `chunk` trial
- * slots, which profilers can inspect kernel by kernel).
+ * slots, which profilers can inspect kernel by kernel), eps_inf (tolerance
+ * of the infeasibility tests on l_inf-normalised directions; 0 = 1e-5),
+ * anderson (1, the default: Anderson acceleration of the multipliers and the
+ * proximal center once the primal test holds on consecutive outer
+ * iterations; 0 = off), anderson_mem (stored outer iterates, 2..5),
+ * controller / ctrl_explore / ctrl_seed (see pdnqp_set_controller).
+ * Read-only names for pdnqp_get_param: gamma, precision, ruiz_outer,
+ * create_prepare_seconds and create_setup_seconds (wall time of
+ * pdnqp_create's host preparation and device setup).
  * Returns PDNQP_ERR_ARG for an unknown name or an out-of-range value. */
 PDNQP_API int pdnqp_set_param(pdnqp_t *h, const char *name, double value);
 PDNQP_API int pdnqp_get_param(const pdnqp_t *h, const char *name, double *value);
