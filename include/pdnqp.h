@@ -304,8 +304,8 @@ PDNQP_API int pdnqp_mlp_wmse(const float *y, const float *target, const float *w
                              float *loss, void *stream);
 /* grad[5378] = dL/dtheta for dL/dy = dy, through the BF16 weights, using the
  * cache of the forward pass.  scratch holds ceil(batch / 16) x 5378 floats
- * of per-block partial gradients (batch <= 16384); the sum over blocks runs
- * in a fixed order, so the result is deterministic. */
+ * of per-block partial gradients (batch <= 1,048,576); the sum over blocks
+ * runs in a fixed order, so the result is deterministic. */
 PDNQP_API int pdnqp_mlp_backward(const uint16_t *w_bf16, const float *x, const float *cache, const float *dy,
                                  int batch, float *grad, float *scratch, void *stream);
 /* One Adam step (bias-corrected, step >= 1) on the FP32 master weights w with

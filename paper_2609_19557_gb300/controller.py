@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
 import time
 
 import numpy as np
@@ -120,16 +121,26 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-4)
     ap.add_argument("--time-limit", type=float, default=60.0)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--data", default=None, help="transitions file (.npz): loaded if present, else written")
     a = ap.parse_args()
     P.load()
     rng = np.random.default_rng(np.random.SeedSequence([2024, 7]))
-    data, t0 = [], time.perf_counter()
-    for i in range(a.train):
-        n = int(rng.integers(a.n_min, a.n_max + 1))
-        _, tr = run(make_instance(10_000 + i, n), eps=a.eps, explore=a.explore, seed=i, time_limit=a.time_limit)
-        data += transitions(tr)
+    t0 = time.perf_counter()
+    if a.data and os.path.exists(a.data):
+        z = np.load(a.data)
+        feats, acts, scores = z["feats"], z["acts"], z["scores"]
+        for _ in range(a.train):  # keep the evaluation sizes of a fresh run
+            rng.integers(a.n_min, a.n_max + 1)
+    else:
+        data = []
+        for i in range(a.train):
+            n = int(rng.integers(a.n_min, a.n_max + 1))
+            _, tr = run(make_instance(10_000 + i, n), eps=a.eps, explore=a.explore, seed=i, time_limit=a.time_limit)
+            data += transitions(tr)
+        feats, acts, scores = (np.array(v) for v in zip(*data))
+        if a.data:
+            np.savez(a.data, feats=feats, acts=acts, scores=scores)
     gen_s = time.perf_counter() - t0
-    feats, acts, scores = zip(*data)
     theta, hist = train(feats, acts, scores)
     if a.out:
         np.save(a.out, theta)
@@ -142,7 +153,7 @@ def main():
         rows.append({"n": n, **{f"rule_{k}": base[k] for k in ("status", "outer", "inner", "seconds", "rel_kkt")},
                      **{f"mlp_{k}": ctrl[k] for k in ("status", "outer", "inner", "seconds", "rel_kkt",
                                                       "ctrl_used", "ctrl_fallbacks")}})
-    print(json.dumps({"trajectories": a.train, "transitions": len(data), "generation_s": gen_s,
+    print(json.dumps({"trajectories": a.train, "transitions": len(scores), "generation_s": gen_s,
                       "loss": hist, "eval": rows}, default=float))
 
 

@@ -26,7 +26,7 @@ constexpr int oW1 = 0, oB1 = oW1 + kHid * kIn, oW2 = oB1 + kHid, oB2 = oW2 + kHi
               oB3 = oW3 + kOut * kHid, kParams = oB3 + kOut;
 constexpr int kCache = 2 * kHid;       // z1, z2 per sample
 constexpr int kSamplesPerBlock = 16;   // samples handled by one block
-constexpr int kMaxGradBlocks = 1024;   // partial-gradient rows
+constexpr int kMaxGradBlocks = 1 << 16;  // partial-gradient rows (batches up to 1,048,576 samples)
 
 static thread_local std::string g_mlp_err;
 
@@ -227,7 +227,7 @@ int pdnqp_mlp_backward(const uint16_t *w_bf16, const float *x, const float *cach
   using namespace pdq;
   if (!w_bf16 || !x || !cache || !dy || !grad || !scratch || batch < 0) return fail("NULL argument");
   const int nb = blocks_for(batch);
-  if (nb > kMaxGradBlocks) return fail("batch too large for the partial-gradient scratch (1024 x 16 samples)");
+  if (nb > kMaxGradBlocks) return fail("batch too large (at most 65536 x 16 samples)");
   cudaStream_t s = (cudaStream_t)stream;
   if (batch == 0) return cudaMemsetAsync(grad, 0, sizeof(float) * kParams, s) == cudaSuccess ? 0 : PDNQP_ERR_CUDA;
   k_mlp_backward<<<nb, kHid, 0, s>>>((const __nv_bfloat16 *)w_bf16, x, cache, dy, batch, scratch);
