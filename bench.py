@@ -269,13 +269,24 @@ def run_native(args):
 
     ttk = None
     if args.ttk > 0 and rank == 0:
-        h3 = P.create_from_instance(inst, precision=args.precision, stream=stream.cuda_stream)
-        P.pdnqp_set_param(h3, "time_limit", args.ttk)
-        st = P.pdnqp_solve(h3, 1e-4, 1e-4)
-        _, _, r3 = P.pdnqp_get(h3)
-        ttk = {"status": P.STATUS_NAMES[st], "seconds": r3["solve_seconds"], "rel_kkt": r3["rel_kkt"],
-               "outer_iters": r3["outer_iters"], "inner_iters": r3["inner_iters"]}
-        h3.close()
+        # Time to relative KKT 1e-4 (capped at --ttk seconds each): the FP32-bulk
+        # form with the trained controller (when its weights are present) and
+        # the plain FP64 form with the paper's rules.
+        ttk = {}
+        wpath = os.path.join(ROOT, "paper_2609_19557_gb300", "controller_weights.npy")
+        legs = [("fp32_controller" if os.path.exists(wpath) else "fp32", 32, os.path.exists(wpath)),
+                ("fp64_plain", 64, False)]
+        for name, prec, use_ctrl in legs:
+            h3 = P.create_from_instance(inst, precision=prec, stream=stream.cuda_stream)
+            P.pdnqp_set_param(h3, "time_limit", args.ttk)
+            if use_ctrl:
+                P.pdnqp_set_controller(h3, np.load(wpath))
+                P.pdnqp_set_param(h3, "controller", 1)
+            st = P.pdnqp_solve(h3, 1e-4, 1e-4)
+            _, _, r3 = P.pdnqp_get(h3)
+            ttk[name] = {"status": P.STATUS_NAMES[st], "seconds": r3["solve_seconds"], "rel_kkt": r3["rel_kkt"],
+                         "outer_iters": r3["outer_iters"], "inner_iters": r3["inner_iters"]}
+            h3.close()
 
     cpu = None
     if rank == 0 and not args.no_cpu:
