@@ -212,17 +212,28 @@ static void transpose(int rows, int cols, const std::vector<int> &rp, const std:
       });
     for (auto &x : th) x.join();
   }
-  // offsets: column c starts at trp[c]; within it, thread t's entries follow thread t-1's
-  long long acc = 0;
-  for (int c = 0; c < cols; ++c) {
-    trp[c] = (int)acc;
-    for (int t = 0; t < T; ++t) {
-      const int k = cnt[t][c];
-      cnt[t][c] = (int)acc;
-      acc += k;
+  // offsets: column c starts at trp[c]; within it, thread t's entries follow
+  // thread t-1's (column totals and per-thread offsets in parallel over
+  // column ranges, the prefix over columns in between)
+  std::vector<int> tot(cols, 0);
+  parallel_for(cols, [&](long long c0, long long c1, int) {
+    for (long long c = c0; c < c1; ++c) {
+      int a = 0;
+      for (int t = 0; t < T; ++t) a += cnt[t][c];
+      tot[c] = a;
     }
-  }
-  trp[cols] = (int)acc;
+  });
+  for (int c = 0; c < cols; ++c) trp[c + 1] = trp[c] + tot[c];
+  parallel_for(cols, [&](long long c0, long long c1, int) {
+    for (long long c = c0; c < c1; ++c) {
+      int acc = trp[c];
+      for (int t = 0; t < T; ++t) {
+        const int k = cnt[t][c];
+        cnt[t][c] = acc;
+        acc += k;
+      }
+    }
+  });
   {
     std::vector<std::thread> th;
     for (int t = 0; t < T; ++t)
