@@ -37,8 +37,12 @@ constexpr int P_CK_R = 8;    // check, row kernel: 16 quantities
 constexpr int P_CK_C = 24;   // check, column kernel: 16 quantities
 constexpr unsigned CK_MAXMASK = 0x0F0Fu;  // quantities 0-3 and 8-11 of a check are maxima
 // Counter words (d.ctr): [0] column last-block counter, [1] check last-block
-// counter, [kCtrBar, kCtrBar + kBarWords) the grid barrier of the persistent loop.
+// counter, [2] row last-block counter (long rows), [kCtrBar, kCtrBar + kBarWords) the grid barrier of the persistent loop.
 constexpr int kCtrBar = 128, kCtrWords = kCtrBar + kBarWords;
+// Rows of A with more entries than this are treated as dense coupling rows
+// (at most kMaxLong of them, the longest first; the rest stay row-wise).
+constexpr int kLongRowMin = 1024;
+constexpr int kMaxLong = 64;
 
 template <typename T>
 struct Mat {
@@ -72,6 +76,20 @@ struct Dev {
   const double *xb, *yb, *sb, *rb;  // base: outer x, inner y, warm-start s and r
   const double *lam, *sig;          // multipliers and row penalties
   double *part;
+  // Dense coupling rows (more than kLongRowMin entries): their products are
+  // split evenly over the blocks of the row pass, and the block that
+  // arrives last combines the block partials in block order and updates
+  // those rows.  As is A with these rows emptied (As == A when nlr == 0).
+  int nlr;
+  int lr_nnz;
+  Mat<T> As;
+  const int *lr_row;   // [nlr] row index of each long row (ascending)
+  const int *lr_ptr;   // [nlr + 1] offsets into lr_ci / lr_val
+  const int *lr_ci;
+  const T *lr_val;
+  const unsigned char *lr_flag;  // [m] 1 for a long row
+  double *lr_part;     // [kMaxLong][kMaxBlocks] block partial products
+  double *lr_acc;      // [4] acceptance-sum terms of the long rows (added to the row sums)
   DevState *st;
   unsigned *ctr;   // arrival counters of the last-block reductions (reset by the last block)
   unsigned long long *ptime;  // persistent loop: ns spent in the primal, row and column(+decision) passes
@@ -139,8 +157,8 @@ __device__ __forceinline__ void stop_loop(cudaGraphConditionalHandle hw, cudaGra
 }
 
 template <bool COND>
-__device__ void decide_body(DevState *stg, const double *part, int nb_r, int nb_c, cudaGraphConditionalHandle hw,
-                            cudaGraphConditionalHandle hc);
+__device__ void decide_body(DevState *stg, const double *part, const double *lacc, int nb_r, int nb_c,
+                            cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hc);
 template <bool COND>
 __device__ void check_final_body(DevState *stg, const double *part, int nb_r, int nb_c,
                                  cudaGraphConditionalHandle hw);
@@ -252,6 +270,125 @@ __global__ void __launch_bounds__(kBlock) k_primal(Dev<T> d) {
   primal_phase<T>(d, d.st);
 }
 
+// ---------------------------------------------------------------------------
+// Dense coupling rows.  Block b of the row pass forms the products of entries
+// [b L / nb, (b + 1) L / nb) of the concatenated long rows (L entries in all)
+// and stores one partial per long row it touches (FP64, block order fixed);
+// the block that arrives last sums, for each long row, the partials of the
+// blocks whose range overlaps it, in block order, and applies the row update
+// of the trial to those rows.  Deterministic for a given grid size.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long lr_cut(long long L, int b, int nb) { return L * b / nb; }
+
+// Sum of one double per thread, in a fixed order; the result is in thread 0.
+__device__ __forceinline__ double block_sum_fixed(double v) {
+  __shared__ double ws[kBlock / 32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double a = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kBlock / 32; ++w) a += ws[w];
+  __syncthreads();
+  return a;
+}
+
+template <typename T>
+__device__ __forceinline__ void long_rows_partial(const Dev<T> &d, const T *xt) {
+  const long long L = d.lr_nnz;
+  const int nb = gridDim.x, b = blockIdx.x;
+  const long long e0 = lr_cut(L, b, nb), e1 = lr_cut(L, b + 1, nb);
+  if (e0 >= e1) return;
+  int s = 0;
+  while (s + 1 < d.nlr && d.lr_ptr[s + 1] <= e0) ++s;
+  for (; s < d.nlr && d.lr_ptr[s] < e1; ++s) {
+    const long long a0 = e0 > d.lr_ptr[s] ? e0 : d.lr_ptr[s];
+    const long long a1 = e1 < d.lr_ptr[s + 1] ? e1 : d.lr_ptr[s + 1];
+    T acc = T(0);
+    for (long long k = a0 + threadIdx.x; k < a1; k += kBlock) acc += d.lr_val[k] * __ldcg(xt + d.lr_ci[k]);
+    const double v = block_sum_fixed(double(acc));
+    if (threadIdx.x == 0) d.lr_part[(long long)s * kMaxBlocks + b] = v;
+  }
+}
+
+// Row update of one constraint row with (A x_tr)_j = ax: the same arithmetic
+// as the row passes below (one thread).
+template <typename T>
+__device__ __forceinline__ void row_update_one(const Dev<T> &d, const DevState *st, long long j, T ax, T &Lt, T &Le,
+                                               T &RH, T &RB) {
+  const int cur = st->cur, nx = 1 - cur, a0 = st->acur, acc = st->accepted;
+  const double t = (double)st->t;
+  const T alpha = T(2.0 / (t + 2.0)), oma = T(1) - alpha;
+  const T beta = T(t / (t + 1.0));
+  const T sct = T(st->kappa / st->omega), sce = T(st->kappa * st->omega);
+  const T ap = T(st->alpha_acc), omap = T(1) - ap;
+  const bool ineq = j >= d.mE;
+  const T y = d.y[cur][j], r = d.r[cur][j];
+  T rb;
+  if (acc) {
+    rb = omap * d.rbar[a0][j] + ap * r;
+    d.rbar[a0 ^ 1][j] = rb;
+    d.ybar[a0 ^ 1][j] = omap * d.ybar[a0][j] + ap * y;
+    if (ineq) d.sbar[a0 ^ 1][j] = omap * d.sbar[a0][j] + ap * d.s[cur][j];
+  } else {
+    rb = d.rbar[a0][j];
+  }
+  const T sig = T(d.sig[j]);
+  const T rt = r - (sct * d.taur[j]) * (d.qr[j] + sig * (oma * rb + alpha * r) + y);
+  d.r[nx][j] = rt;
+  T bwt = ax - rt, ds = T(0);
+  if (ineq) {
+    const T s0 = d.s[cur][j];
+    const T stv = clampv<T>(s0 - (sct * d.taus[j]) * (d.qs[j] + y), d.ls[j], d.us[j]);
+    d.s[nx][j] = stv;
+    ds = stv - s0;
+    Lt += ds * ds * d.itaus[j];
+    bwt -= stv;
+  }
+  const T yt = y + (sce * d.eta[j]) * (d.hp[j] - bwt - beta * (bwt - d.Bw[cur][j]));
+  d.Bw[nx][j] = bwt;
+  d.y[nx][j] = yt;
+  const T dr = rt - r, dyv = yt - y;
+  Lt += dr * dr * d.itaur[j];
+  Le += dyv * dyv * d.ieta[j];
+  RH += fabs(dr * sig * dr);
+  RB += fabs(ds * dyv) + fabs(dr * dyv);
+}
+
+// Run by one whole block once every block's partials are visible (nb = the
+// row pass's grid size).  Warp w takes long rows w, w + 8, ...; the four
+// acceptance-sum terms go to lr_acc (warps combined in order).
+template <typename T>
+__device__ void long_rows_finish(const Dev<T> &d, const DevState *st, int nb) {
+  __shared__ double wacc[kBlock / 32][4];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long L = d.lr_nnz;
+  T Lt = T(0), Le = T(0), RH = T(0), RB = T(0);
+  for (int s = w; s < d.nlr; s += kBlock / 32) {
+    const long long p0 = d.lr_ptr[s], p1 = d.lr_ptr[s + 1];
+    double a = 0.0;
+    for (int b = lane; b < nb; b += 32) {
+      const long long e0 = lr_cut(L, b, nb), e1 = lr_cut(L, b + 1, nb);
+      if (e0 < e1 && e0 < p1 && e1 > p0) a += __ldcg(d.lr_part + (long long)s * kMaxBlocks + b);
+    }
+    a = warp_sum(a);
+    if (lane == 0) row_update_one<T>(d, st, d.lr_row[s], T(a), Lt, Le, RH, RB);
+  }
+  if (lane == 0) {
+    wacc[w][0] = double(Lt);
+    wacc[w][1] = double(Le);
+    wacc[w][2] = double(RH);
+    wacc[w][3] = double(RB);
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double v = 0.0;
+    for (int k = 0; k < kBlock / 32; ++k) v += wacc[k][threadIdx.x];
+    d.lr_acc[threadIdx.x] = v;
+  }
+  __syncthreads();
+}
+
 // Constraint rows: (A x_tr)_j, the s/r blocks of the primal trial, B w_tr,
 // the dual trial y_tr = y + eta (h - B w_tr - beta (B w_tr - B w)), and the
 // row-local terms of the acceptance sums.  Steps are used as
@@ -271,7 +408,7 @@ __device__ __forceinline__ void rows_phase(const Dev<T> &d, const DevState *st) 
   TileIter ti;
   for (long long tile = ti.first; tile < d.m; tile += ti.step) {
     const long long j = tile + ti.lane;
-    const bool valid = j < d.m, ineq = j >= d.mE;
+    const bool valid = j < d.m && !(d.nlr && d.lr_flag[j]), ineq = j >= d.mE;
     // Everything that does not need (A x_tr)_j first (the r and s blocks of
     // the trial and the operands of the dual step), so that these loads
     // overlap the SpMV chain.
@@ -302,7 +439,7 @@ __device__ __forceinline__ void rows_phase(const Dev<T> &d, const DevState *st) 
       etj = d.eta[j];
       hpj = d.hp[j];
     }
-    const T ax = tile_row_sum<G, T>(d.A.rp, d.A.ci, d.A.val, tile, d.m, [&](int k, T a) { return a * __ldcg(xt + k); });
+    const T ax = tile_row_sum<G, T>(d.As.rp, d.As.ci, d.As.val, tile, d.m, [&](int k, T a) { return a * __ldcg(xt + k); });
     if (valid) {
       T bwt = ax - rt;
       if (ineq) bwt -= stv;
@@ -323,7 +460,12 @@ __device__ __forceinline__ void rows_phase(const Dev<T> &d, const DevState *st) 
 template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_rows(Dev<T> d) {
   if (d.st->status != ST_RUNNING) return;
+  if (d.nlr) long_rows_partial<T>(d, d.x[1 - d.st->cur]);
   rows_phase<T, G>(d, d.st);
+  if (d.nlr && arrive_last(d.ctr + 2)) {
+    long_rows_finish<T>(d, d.st, gridDim.x);
+    if (threadIdx.x == 0) d.ctr[2] = 0u;
+  }
 }
 
 // Variable rows: (H x_tr)_i and (A' y_tr)_i (the products with Q and A^T),
@@ -373,7 +515,7 @@ __global__ void __launch_bounds__(kBlock) k_cols(Dev<T> d, int nb_r) {
   }
   cols_phase<T, G, G>(d, d.st);
   if (arrive_last(d.ctr)) {
-    decide_body<COND>(d.st, d.part, nb_r, gridDim.x, d.hw, d.hc);
+    decide_body<COND>(d.st, d.part, d.nlr ? d.lr_acc : nullptr, nb_r, gridDim.x, d.hw, d.hc);
     if (threadIdx.x == 0) d.ctr[0] = 0u;
   }
 }
@@ -578,10 +720,28 @@ __device__ __forceinline__ bool stream_panels(StreamCtl &ctl, unsigned char *buf
           sum[m] = a;
         }
       } else {
+        // The panel does not fit a stage: read it from global memory.  Rows of
+        // at most kLongRow entries are summed by their own lane in entry order;
+        // longer rows (dense coupling rows) by the whole warp, lane-strided,
+        // then a fixed butterfly (deterministic).
+        constexpr int kLongRow = 64;
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
+          const bool lng = valid && re[m] - rb[m] > kLongRow;
           T a = T(0);
-          for (int k2 = rb[m]; k2 < re[m]; ++k2) a += M[m].val[k2] * __ldcg(gx[m] + M[m].ci[k2]);
+          if (!lng)
+            for (int k2 = rb[m]; k2 < re[m]; ++k2) a += M[m].val[k2] * __ldcg(gx[m] + M[m].ci[k2]);
+          unsigned todo = __ballot_sync(0xffffffffu, lng);
+          while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int b = __shfl_sync(0xffffffffu, rb[m], l), e = __shfl_sync(0xffffffffu, re[m], l);
+            T w = T(0);
+            for (int k2 = b + lane; k2 < e; k2 += 32) w += M[m].val[k2] * __ldcg(gx[m] + M[m].ci[k2]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+            if (lane == l) a = w;
+          }
           sum[m] = a;
         }
       }
@@ -619,7 +779,7 @@ __device__ __forceinline__ bool stream_panels(StreamCtl &ctl, unsigned char *buf
 
 // Row pass of the persistent loop: the per-row arithmetic of rows_phase with
 // (A x_tr) from the panel stream.
-template <typename T>
+template <typename T, bool LR>
 __device__ __forceinline__ bool rows_phase_stream(const Dev<T> &d, const DevState *st, StreamCtl &ctl,
                                                   unsigned char *buf, unsigned &ph, unsigned *fault) {
   const int cur = st->cur, nx = 1 - cur, a0 = st->acur, acc = st->accepted;
@@ -633,7 +793,8 @@ __device__ __forceinline__ bool rows_phase_stream(const Dev<T> &d, const DevStat
     T y, r, rb, yb, tr, qr, bw, eta, hp, itr, ie, s, sb, ts, qs, ls, us, its;
     double sig;
   };
-  const Mat<T> M[1] = {d.A};
+  if (LR) long_rows_partial<T>(d, d.x[nx]);
+  const Mat<T> M[1] = {d.As};
   const T *gx[1] = {d.x[nx]};
   const bool ok = stream_panels<T, 1, 8>(
       ctl, buf, ph, fault, M, gx, d.m,
@@ -666,7 +827,7 @@ __device__ __forceinline__ bool rows_phase_stream(const Dev<T> &d, const DevStat
         return c;
       },
       [&](long long j, bool valid, const Raw &c, const T *sum) {
-        if (!valid) return;
+        if (!valid || (LR && d.lr_flag[j])) return;
         const bool ineq = j >= d.mE;
         T rb = c.rb;
         if (acc) {  // running averages of the previous acceptance
@@ -750,7 +911,9 @@ __device__ __forceinline__ bool cols_phase_stream(const Dev<T> &d, const DevStat
 // while a check is pending (the check kernels clear check_due).  All blocks
 // take the same branches (the state is block-uniform), so every barrier is
 // reached by every block.  Partial sums use this grid's size for both passes.
-template <typename T>
+// LR: the instance has dense coupling rows (d.nlr > 0); a separate
+// instantiation keeps their branches out of the common case.
+template <typename T, bool LR>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 2) k_trials(Dev<T> d) {
   __shared__ DevState S;
   __shared__ StreamCtl ctl;
@@ -779,13 +942,16 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 2) k_trials(Dev<T
     lap(0);
     if (!grid_sync(bar)) return;
     lap(1);
-    if (!rows_phase_stream<T>(d, &S, ctl, stage_buf, ph, fault)) return;
+    if (!rows_phase_stream<T, LR>(d, &S, ctl, stage_buf, ph, fault)) return;
     lap(2);
-    if (!grid_sync(bar)) return;
+    if (!grid_sync(bar, [&] {
+          if (LR) long_rows_finish<T>(d, &S, nb);
+        }))
+      return;
     lap(3);
     if (!cols_phase_stream<T>(d, &S, ctl, stage_buf, ph, fault)) return;
     lap(4);
-    if (!grid_sync(bar, [&] { decide_body<false>(d.st, d.part, nb, nb, 0, 0); })) return;
+    if (!grid_sync(bar, [&] { decide_body<false>(d.st, d.part, LR ? d.lr_acc : nullptr, nb, nb, 0, 0); })) return;
     state_load(S, d.st);
     lap(5);
   }
@@ -837,8 +1003,8 @@ __device__ __forceinline__ void decide_logic(DevState *st, const double (&a)[4],
 }
 
 template <bool COND>
-__device__ void decide_body(DevState *stg, const double *part, int nb_r, int nb_c, cudaGraphConditionalHandle hw,
-                            cudaGraphConditionalHandle hc) {
+__device__ void decide_body(DevState *stg, const double *part, const double *lacc, int nb_r, int nb_c,
+                            cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hc) {
   __shared__ DevState S;
   state_load(S, stg);
   double a[4], b[4];
@@ -854,6 +1020,8 @@ __device__ void decide_body(DevState *stg, const double *part, int nb_r, int nb_
     final_reduce<4>(part + P_TR_R * kMaxBlocks, nb_r, 0u, a);
     final_reduce<4>(part + P_TR_C * kMaxBlocks, nb_c, 0u, b);
   }
+  if (lacc)
+    for (int k = 0; k < 4; ++k) a[k] += __ldcg(lacc + k);
   if (threadIdx.x == 0) {
     decide_logic(&S, a, b);
     if (COND) {

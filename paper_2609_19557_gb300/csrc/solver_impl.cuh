@@ -381,7 +381,7 @@ class Solver : public SolverBase {
     k_add_diag<<<grid_n(), kBlock, 0, s_>>>(n_, qdiag_, qv_, 1.0 / gamma_);
     PDNQP_CK(cudaGetLastError());
     // ---- T-typed copies and inner vectors
-    PDNQP_TRY(alloc_T());
+    PDNQP_TRY(alloc_T(P.a_rp));
     PDNQP_CK(cudaStreamSynchronize(s_));
     ready_ = true;
     return 0;
@@ -468,7 +468,7 @@ class Solver : public SolverBase {
     return reduce_to_host(1, nb, 0u, out);
   }
 
-  int alloc_T() {
+  int alloc_T(const std::vector<int> &arp) {
     Dev<T> &d = d_;
     d.n = n_;
     d.m = m_;
@@ -491,6 +491,7 @@ class Solver : public SolverBase {
       d.A = {Ad_.nrows, Ad_.rp, Ad_.ci, av};
       d.At = {Atd_.nrows, Atd_.rp, Atd_.ci, atv};
     }
+    PDNQP_TRY(split_long_rows(arp));
     for (int b = 0; b < 2; ++b) {
       PDNQP_TRY(dalloc(&d.x[b], n_));
       PDNQP_TRY(dalloc(&d.Hx[b], n_));
@@ -540,6 +541,78 @@ class Solver : public SolverBase {
     return 0;
   }
 
+  // Dense coupling rows of A (more than kLongRowMin entries; the kMaxLong
+  // longest when there are more): copies of their entries in row order for
+  // the split products, and As = A with those rows emptied for the row-wise
+  // passes of the trial.  Device-to-device copies of contiguous runs, after
+  // the values were scaled and converted.
+  int split_long_rows(const std::vector<int> &arp) {
+    Dev<T> &d = d_;
+    d.nlr = 0;
+    d.lr_nnz = 0;
+    d.As = d.A;
+    d.lr_row = d.lr_ptr = d.lr_ci = nullptr;
+    d.lr_val = nullptr;
+    d.lr_flag = nullptr;
+    d.lr_part = d.lr_acc = nullptr;
+    auto len = [&](int j) { return arp[j + 1] - arp[j]; };
+    std::vector<int> lr;
+    for (int j = 0; j < m_; ++j)
+      if (len(j) > kLongRowMin) lr.push_back(j);
+    if (lr.empty()) return 0;
+    if ((int)lr.size() > kMaxLong) {
+      std::stable_sort(lr.begin(), lr.end(), [&](int a, int b) { return len(a) > len(b); });
+      lr.resize(kMaxLong);
+      std::sort(lr.begin(), lr.end());
+    }
+    const int nl = (int)lr.size();
+    std::vector<int> lptr(nl + 1, 0), srp(m_ + 1, 0);
+    std::vector<unsigned char> flag(m_, 0);
+    for (int k = 0; k < nl; ++k) {
+      lptr[k + 1] = lptr[k] + len(lr[k]);
+      flag[lr[k]] = 1;
+    }
+    for (int j = 0; j < m_; ++j) srp[j + 1] = srp[j] + (flag[j] ? 0 : len(j));
+    int *lrow, *lp, *lci, *srpd, *sci;
+    unsigned char *lflag;
+    T *lval, *sval;
+    PDNQP_TRY(upload(&lrow, lr));
+    PDNQP_TRY(upload(&lp, lptr));
+    PDNQP_TRY(upload(&lflag, flag));
+    PDNQP_TRY(upload(&srpd, srp));
+    PDNQP_TRY(dalloc(&lci, lptr[nl]));
+    PDNQP_TRY(dalloc(&lval, lptr[nl]));
+    PDNQP_TRY(dalloc(&sci, srp[m_]));
+    PDNQP_TRY(dalloc(&sval, srp[m_]));
+    for (int k = 0; k < nl; ++k) {
+      const size_t c = (size_t)len(lr[k]);
+      PDNQP_CK(cudaMemcpyAsync(lci + lptr[k], d.A.ci + arp[lr[k]], c * sizeof(int), cudaMemcpyDeviceToDevice, s_));
+      PDNQP_CK(cudaMemcpyAsync(lval + lptr[k], d.A.val + arp[lr[k]], c * sizeof(T), cudaMemcpyDeviceToDevice, s_));
+    }
+    // Runs of ordinary rows between the long ones.
+    for (int j0 = 0, k = 0; j0 < m_; ++k) {
+      const int j1 = k < nl ? lr[k] : m_;
+      const size_t c = (size_t)(arp[j1] - arp[j0]);
+      if (c) {
+        PDNQP_CK(cudaMemcpyAsync(sci + srp[j0], d.A.ci + arp[j0], c * sizeof(int), cudaMemcpyDeviceToDevice, s_));
+        PDNQP_CK(cudaMemcpyAsync(sval + srp[j0], d.A.val + arp[j0], c * sizeof(T), cudaMemcpyDeviceToDevice, s_));
+      }
+      j0 = j1 + 1;
+    }
+    PDNQP_TRY(dalloc(&d.lr_part, (size_t)kMaxLong * kMaxBlocks));
+    PDNQP_TRY(dalloc(&d.lr_acc, 4));
+    PDNQP_CK(cudaMemsetAsync(d.lr_acc, 0, 4 * sizeof(double), s_));
+    d.nlr = nl;
+    d.lr_nnz = lptr[nl];
+    d.lr_row = lrow;
+    d.lr_ptr = lp;
+    d.lr_ci = lci;
+    d.lr_val = lval;
+    d.lr_flag = lflag;
+    d.As = {m_, srpd, sci, sval};
+    return 0;
+  }
+
   // ------------------------------------------------------- launchers
   // Tile kernels: one warp per 32 rows and trip, kBlock / 32 warps per block.
   int nb_rows() const { return grid_for(std::max(m_, 1), kBlock); }
@@ -573,6 +646,8 @@ class Solver : public SolverBase {
     launch_trial();
     launch_check_group();
   }
+  // The persistent loop with or without the dense-coupling-row split.
+  void (*trials_fn() const)(Dev<T>) { return d_.nlr ? k_trials<T, true> : k_trials<T, false>; }
   // Persistent trial loop: one cooperative launch per slot, grid = the
   // co-resident block count (capped by the work), each launch bracketed by a
   // pair of events so the loop's device time is measured on its own stream.
@@ -585,12 +660,12 @@ class Solver : public SolverBase {
     if (cudaDeviceGetAttribute(&can, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !can) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     const int smem = (int)stream_smem_bytes<T>();
-    if (cudaFuncSetAttribute(k_trials<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+    if (cudaFuncSetAttribute(trials_fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trials<T>, kBlock, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trials_fn(), kBlock, smem) != cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
@@ -606,7 +681,7 @@ class Solver : public SolverBase {
     }
     PDNQP_CK(cudaEventRecord(loop_ev_[2 * slot], s_));
     void *args[] = {(void *)&d_};
-    PDNQP_CK(cudaLaunchCooperativeKernel((const void *)k_trials<T>, dim3(nb), dim3(kBlock), args,
+    PDNQP_CK(cudaLaunchCooperativeKernel((const void *)trials_fn(), dim3(nb), dim3(kBlock), args,
                                          stream_smem_bytes<T>(), s_));
     PDNQP_CK(cudaEventRecord(loop_ev_[2 * slot + 1], s_));
     return 0;

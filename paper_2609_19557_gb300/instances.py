@@ -33,7 +33,8 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse as sp
 
-WORKLOAD_CODES = {"small": 0, "mid": 1, "large": 2, "batched": 3, "learned": 4, "clique": 5}
+WORKLOAD_CODES = {"small": 0, "mid": 1, "large": 2, "batched": 3, "learned": 4, "clique": 5,
+                  "softlabel": 11, "flow": 12, "svm": 13}
 
 
 def _rng(seed: int, code: int) -> np.random.Generator:
@@ -239,9 +240,23 @@ def large_qp(seed: int = 0, n: int = 1_000_000, m: int = 500_000, a_per_row: int
 def clique_qp(seed: int = 0, n: int = 60, p: float = 0.1) -> dict:
     """Motzkin-Straus QP on G(n, p): min -x'A_G x s.t. sum(x) = 1, x >= 0 (Q = -2 A_G)."""
     rng = _rng(seed, WORKLOAD_CODES["clique"])
-    iu = np.triu_indices(n, 1)
-    mask = rng.random(iu[0].size) < p
-    r, cc = iu[0][mask], iu[1][mask]
+    if n <= 2000:
+        iu = np.triu_indices(n, 1)
+        mask = rng.random(iu[0].size) < p
+        r, cc = iu[0][mask], iu[1][mask]
+    else:
+        # Large graphs: a Binomial number of edges, then distinct uniform
+        # pairs i < j (the same distribution as the pairwise draws above).
+        npairs = n * (n - 1) // 2
+        k = int(rng.binomial(npairs, p))
+        keys = np.unique(rng.integers(0, npairs, size=int(k * 1.1) + 16))
+        while keys.size < k:
+            keys = np.unique(np.concatenate([keys, rng.integers(0, npairs, size=k - keys.size + 16)]))
+        keys = rng.permutation(keys)[:k]
+        # Pair index -> (i, j), i < j, row-major over the upper triangle.
+        i = (n - 2 - np.floor(np.sqrt(-8.0 * keys + 4.0 * n * (n - 1) - 7) / 2.0 - 0.5)).astype(np.int64)
+        j = (keys + i + 1 - n * (n - 1) // 2 + (n - i) * ((n - i) - 1) // 2).astype(np.int64)
+        r, cc = i, j
     G = sp.coo_matrix((np.ones(r.size), (r, cc)), shape=(n, n))
     AG = (G + G.T).tocsr()
     Q = (-2.0 * AG).tocsr()
@@ -276,8 +291,9 @@ def tiny_qp(seed: int, n: int = 4, m: int = 2, convex: bool = False, eq_rows: in
 
 
 def make(workload: str, seed: int = 0, **kw) -> dict:
-    """Instance by workload name ("small", "mid", "large", "clique", "tiny")."""
-    fn = {"small": small_qp, "mid": mid_qp, "large": large_qp, "clique": clique_qp, "tiny": tiny_qp}[workload]
+    """Instance by workload name ("small", "mid", "large", "clique", "tiny", "softlabel", "flow", "svm")."""
+    fn = {"small": small_qp, "mid": mid_qp, "large": large_qp, "clique": clique_qp, "tiny": tiny_qp,
+          "softlabel": softlabel_qp, "flow": flow_qp, "svm": svm_qp}[workload]
     return fn(seed=seed, **kw)
 
 
@@ -320,3 +336,152 @@ def dual_infeasible_qp(seed: int = 0, n: int = 40, m: int = 20) -> dict:
     lo_gap, hi_gap = inst["A"] @ inst["x0"] - inst["l_c"], inst["u_c"] - inst["A"] @ inst["x0"]
     l_c, u_c = ax - lo_gap, ax + hi_gap
     return _pack(Q, inst["c"], A, l_c, u_c, l_x, u_x, x0, workload="dual_inf", seed=seed)
+
+
+# ---------------------------------------------------------------------------
+# The paper's three million-variable model families (Appendix "Million-variable
+# benchmark construction", parameter distributions of Table
+# tab:million-generation, one default_rng stream per scenario; the family
+# codes r = 1, 2, 3 of the paper are 11, 12, 13 here so that the streams do
+# not coincide with those of the other generators).  The
+# paper gives the models and the parameter ranges; how the graph, anchors and
+# reference flows are drawn from those parameters is this module's reading.
+# These are new instances, not the paper's frozen ones.
+# ---------------------------------------------------------------------------
+def _sym_from_upper(n: int, rows: np.ndarray, cols: np.ndarray, vals: np.ndarray) -> sp.csr_matrix:
+    """Symmetric matrix from upper-triangle entries (i < j), mirrored exactly."""
+    U = sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr()
+    U.sum_duplicates()
+    M = (U + U.T).tocsr()
+    M.sort_indices()
+    return M
+
+
+def softlabel_qp(seed: int = 101, n_target: int = 1_000_000) -> dict:
+    """Soft-label graph clustering: min -sum_{ij in E} w~_ij sum_c x_ic x_jc + sum a_ic x_ic
+    s.t. sum_c x_ic = 1, 0 <= x <= 1, (1-delta) N/K <= sum_i x_ic <= (1+delta) N/K."""
+    rng = _rng(seed, WORKLOAD_CODES["softlabel"])
+    K = int(rng.choice([3, 5, 8, 10]))
+    rg = int(rng.integers(8, 25))
+    p_same = rng.uniform(0.55, 0.90)
+    s_cross = rng.uniform(0.08, 0.45)
+    sig_w = rng.uniform(0.10, 0.50)
+    f_anchor = rng.uniform(0.03, 0.20)
+    a_str = rng.uniform(0.5, 2.0)
+    noise = rng.uniform(0.01, 0.08)
+    delta = rng.uniform(0.05, 0.25)
+    N = n_target // K
+    labels = rng.permutation(np.arange(N) % K)  # balanced planted labelling
+    # Reading: every vertex draws rg / 2 partners, of its own class with
+    # probability p_same, otherwise of another class; weights are log-normal,
+    # cross-class ones scaled by s_cross.
+    half = max(1, rg // 2)
+    src = np.repeat(np.arange(N), half)
+    same = rng.random(src.size) < p_same
+    dst = np.empty(src.size, dtype=np.int64)
+    members = [np.flatnonzero(labels == k) for k in range(K)]
+    for k in range(K):
+        own = labels[src] == k
+        m1 = own & same
+        dst[m1] = members[k][rng.integers(0, members[k].size, size=int(m1.sum()))]
+        m2 = own & ~same
+        others = np.flatnonzero(labels != k)
+        dst[m2] = others[rng.integers(0, others.size, size=int(m2.sum()))]
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    w = np.exp(sig_w * rng.standard_normal(src.size)) * np.where(labels[src] == labels[dst], 1.0, s_cross)
+    lo, hi = np.minimum(src, dst), np.maximum(src, dst)
+    U = sp.coo_matrix((w, (lo, hi)), shape=(N, N)).tocsr()
+    U.sum_duplicates()
+    deg = np.asarray((U + U.T).sum(axis=1)).ravel()
+    Uc = U.tocoo()
+    wt = Uc.data / np.sqrt(deg[Uc.row] * deg[Uc.col])  # normalised weight, symmetric by construction
+    Wt = _sym_from_upper(N, Uc.row, Uc.col, wt)
+    Q = (-sp.kron(Wt, sp.identity(K, format="csr"), format="csr")).tocsr()
+    Q.sort_indices()
+    a = noise * rng.standard_normal((N, K))
+    anchors = np.flatnonzero(rng.random(N) < f_anchor)
+    a[anchors, labels[anchors]] -= a_str
+    n = N * K
+    ri = np.concatenate([np.repeat(np.arange(N), K), N + np.tile(np.arange(K), N)])
+    ci = np.concatenate([np.arange(n), np.arange(n)])
+    A = sp.csr_matrix((np.ones(2 * n), (ri, ci)), shape=(N + K, n))
+    A.sort_indices()
+    cap_lo, cap_hi = (1 - delta) * N / K, (1 + delta) * N / K
+    l_c = np.concatenate([np.ones(N), np.full(K, cap_lo)])
+    u_c = np.concatenate([np.ones(N), np.full(K, cap_hi)])
+    return _pack(Q, a.ravel(), A, l_c, u_c, np.zeros(n), np.ones(n), np.full(n, 1.0 / K), workload="softlabel",
+                 seed=seed, K=K, delta=delta, labels=labels)
+
+
+def flow_qp(seed: int = 101, n_target: int = 1_000_000) -> dict:
+    """Concave-cost multistage flow: min sum_e c_e f_e - alpha c_e / u_e f_e^2
+    s.t. B f = b, 0 <= f <= u, on L layers of width w with three carriers."""
+    rng = _rng(seed, WORKLOAD_CODES["flow"])
+    L = int(rng.choice([4, 6, 8, 12, 16]))
+    alpha = rng.uniform(0.03, 0.24)
+    c0 = rng.uniform(0.05, 0.30)
+    rho = rng.uniform(1.05, 1.80)
+    growth = rng.uniform(0.0, 0.12)
+    base = 1.0 / (1.0 - 2.0 * alpha)
+    ratio = rng.uniform(base + 0.25, base + 2.0)  # geometric carrier-cost ratio
+    h_lo, h_hi = rng.uniform(0.30, 1.00), rng.uniform(1.20, 3.00)
+    h = rng.uniform(h_lo, h_hi, size=3)  # carrier reference-flow levels
+    w = max(1, int(round(n_target / (3 * (L - 1)))))
+    tails, heads, cost, f0 = [], [], [], []
+    for stage in range(L - 1):
+        for k in range(3):
+            perm = rng.permutation(w)
+            tails.append(stage * w + np.arange(w))
+            heads.append((stage + 1) * w + perm)
+            cost.append(np.full(w, c0 * ratio ** k * (1.0 + growth) ** stage))
+            # Reading: arc reference flows scatter +-50 % around the carrier level.
+            f0.append(h[k] * rng.uniform(0.5, 1.5, size=w))
+    tails, heads = np.concatenate(tails), np.concatenate(heads)
+    c, f0 = np.concatenate(cost), np.concatenate(f0)
+    u = rho * f0
+    ne, nv = tails.size, w * L
+    B = sp.csr_matrix((np.concatenate([-np.ones(ne), np.ones(ne)]),
+                       (np.concatenate([tails, heads]), np.concatenate([np.arange(ne), np.arange(ne)]))),
+                      shape=(nv, ne))
+    B.sort_indices()
+    b = B @ f0
+    Q = sp.diags(-2.0 * alpha * c / u, format="csr")
+    return _pack(Q, c, B, b, b.copy(), np.zeros(ne), u, f0, workload="flow", seed=seed, L=L, alpha=alpha)
+
+
+def svm_qp(seed: int = 101, n_target: int = 1_000_000) -> dict:
+    """Indefinite graph-kernel SVM: min 1/2 a'Y K_eta Y a - 1'a s.t. y'a = 0,
+    0 <= a <= U_alpha, K_eta = (1 - eta) I + eta D^-1/2 W D^-1/2 on a symmetric
+    k-nearest-neighbour graph with W_ij = |tanh(kappa z_i'z_j / d)|."""
+    from scipy.spatial import cKDTree
+    rng = _rng(seed, WORKLOAD_CODES["svm"])
+    d = int(rng.choice([4, 8, 12, 16]))
+    k = int(rng.choice([6, 8, 12, 16, 24]))
+    chi = rng.uniform(0.75, 3.00)
+    nu = rng.uniform(0.50, 1.25)
+    kappa = rng.uniform(0.75, 3.00)
+    eta = rng.uniform(0.60, 0.97)
+    Ua = rng.uniform(0.25, 2.00)
+    N = n_target
+    y = rng.permutation(np.where(np.arange(N) < N // 2, 1.0, -1.0))
+    z = nu * rng.standard_normal((N, d))
+    z[:, 0] += chi * y
+    z[:, 1:] += 0.15 * rng.standard_normal((N, d - 1))
+    _, nb = cKDTree(z).query(z, k=k + 1)
+    src = np.repeat(np.arange(N), k)
+    dst = nb[:, 1:].ravel()
+    keep = src != dst
+    lo, hi = np.minimum(src[keep], dst[keep]), np.maximum(src[keep], dst[keep])
+    pairs = np.unique(lo * N + hi)  # symmetric kNN graph (union)
+    lo, hi = pairs // N, pairs % N
+    wv = np.abs(np.tanh(kappa * np.einsum("ij,ij->i", z[lo], z[hi]) / d))
+    W = _sym_from_upper(N, lo, hi, wv)
+    deg = np.asarray(W.sum(axis=1)).ravel()
+    deg[deg == 0] = 1.0
+    sv = eta * wv / np.sqrt(deg[lo] * deg[hi]) * y[lo] * y[hi]  # entries of Y K_eta Y off the diagonal
+    Q = (_sym_from_upper(N, lo, hi, sv) + (1.0 - eta) * sp.identity(N, format="csr")).tocsr()
+    Q.sort_indices()
+    A = sp.csr_matrix(y.reshape(1, N))
+    return _pack(Q, -np.ones(N), A, np.zeros(1), np.zeros(1), np.zeros(N), np.full(N, Ua), np.zeros(N),
+                 workload="svm", seed=seed, eta=eta, labels=y)
