@@ -139,6 +139,21 @@ PDNQP_API void pdnqp_destroy(pdnqp_t *h);
  * Calling it again restarts from the start point. */
 PDNQP_API int pdnqp_solve(pdnqp_t *h, double eps_abs, double eps_rel);
 
+/* The batched form: solves `count` independent problems, each with its own
+ * handle (distinct handles; each created on its own stream, which
+ * pdnqp_create does when no stream is given), with per-problem termination
+ * (Eq. outer-termination with eps_abs / eps_rel), restarts and limits.
+ * `threads` host threads (0: min(count, 16)) take the problems largest
+ * first and run pdnqp_solve on them concurrently, so the small inner solves
+ * of different problems overlap on the GPU; every solve runs in the graph
+ * form (the handle's "persistent" parameter is set to 0 for the call and
+ * restored).  status[i] receives pdnqp_solve's return for hs[i]; the results
+ * are read with pdnqp_get per handle.  Returns 0, or the first negative code
+ * of a failed solve (the others still run to the end).  Blocks until all
+ * solves have finished. */
+PDNQP_API int pdnqp_solve_batch(pdnqp_t *const *hs, int count, double eps_abs, double eps_rel, int threads,
+                                int *status);
+
 /* Copies the result of the last pdnqp_solve: x (n entries, original
  * coordinates) and y (m entries, original row order, sign convention of Eq.
  * kkt-stationarity: 0 in Qx + c + A'y + N(x), so y <= 0 on rows active at
@@ -172,10 +187,16 @@ PDNQP_API int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0);
  * anderson (1, the default: Anderson acceleration of the multipliers and the
  * proximal center once the primal test holds on consecutive outer
  * iterations; 0 = off), anderson_mem (stored outer iterates, 2..5),
- * controller / ctrl_explore / ctrl_seed (see pdnqp_set_controller).
+ * controller / ctrl_explore / ctrl_seed (see pdnqp_set_controller),
+ * autotune (1: when the graph form runs and g_rows / g_cols are 0, the first
+ * inner solve times the row and column kernels for 4, 8 and 16 lanes per row
+ * and keeps the fastest for this handle; 0, the default: the mean-row-length
+ * choice).
  * Read-only names for pdnqp_get_param: gamma, precision, ruiz_outer,
  * create_prepare_seconds and create_setup_seconds (wall time of
- * pdnqp_create's host preparation and device setup).
+ * pdnqp_create's host preparation and device setup), lanes_rows and
+ * lanes_cols (the lanes-per-row defaults in use: the setup's choice or the
+ * autotuner's).
  * Returns PDNQP_ERR_ARG for an unknown name or an out-of-range value. */
 PDNQP_API int pdnqp_set_param(pdnqp_t *h, const char *name, double value);
 PDNQP_API int pdnqp_get_param(const pdnqp_t *h, const char *name, double *value);

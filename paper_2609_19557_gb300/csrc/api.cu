@@ -452,6 +452,53 @@ int pdnqp_solve(pdnqp_t *h, double eps_abs, double eps_rel) {
   return rc;
 }
 
+int pdnqp_solve_batch(pdnqp_t *const *hs, int count, double eps_abs, double eps_rel, int threads, int *status) {
+  if (count < 0 || (count > 0 && (!hs || !status))) return fail(nullptr, PDNQP_ERR_ARG, "bad batch arguments");
+  if (!(eps_abs >= 0) || !(eps_rel >= 0)) return fail(nullptr, PDNQP_ERR_ARG, "tolerances must be >= 0");
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i]) return fail(nullptr, PDNQP_ERR_ARG, "batch handle is NULL");
+    for (int k = 0; k < i; ++k)
+      if (hs[k] == hs[i]) return fail(nullptr, PDNQP_ERR_ARG, "batch handles must be distinct");
+  }
+  if (count == 0) return 0;
+  // Largest problems first, so that the long solves start early.
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (long long)hs[a]->n + hs[a]->m > (long long)hs[b]->n + hs[b]->m;
+  });
+  const int nt = std::max(1, std::min(count, threads > 0 ? threads : 16));
+  std::atomic<int> next{0};
+  std::vector<int> rcs(count, 0);
+  std::mutex err_mu;
+  std::string first_err;
+  auto work = [&]() {
+    for (int k; (k = next.fetch_add(1)) < count;) {
+      pdnqp_t *h = hs[order[k]];
+      const int keep = h->prm.persistent;
+      h->prm.persistent = 0;  // graph form: no concurrent cooperative launches
+      const int rc = pdnqp_solve(h, eps_abs, eps_rel);
+      h->prm.persistent = keep;
+      rcs[order[k]] = rc;
+      if (rc < 0) {
+        std::lock_guard<std::mutex> lk(err_mu);
+        if (first_err.empty()) first_err = g_err;
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+  work();
+  for (auto &t : pool) t.join();
+  int worst = 0;
+  for (int i = 0; i < count; ++i) {
+    status[i] = rcs[i];
+    if (rcs[i] < 0 && worst == 0) worst = rcs[i];
+  }
+  if (worst < 0) return fail(nullptr, worst, "batch: " + first_err);
+  return 0;
+}
+
 int pdnqp_get(const pdnqp_t *h, double *x, double *y, pdnqp_residuals *r) {
   if (!h) return fail(nullptr, PDNQP_ERR_ARG, "handle is NULL");
   cudaSetDevice(h->device);
@@ -516,7 +563,7 @@ int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0) {
   X(g_rows, i, 0.0, 16.0) X(g_cols, i, 0.0, 16.0) X(iter_budget, ll, 1.0, 4e18) X(cond_graph, i, 0.0, 1.0) \
   X(persistent, i, 0.0, 1.0) X(loop_blocks_per_sm, i, 0.0, 32.0) X(controller, i, 0.0, 1.0)             \
   X(ctrl_explore, d, 0.0, 10.0) X(ctrl_seed, ll, 0.0, 9.2e18) X(eps_inf, d, 0.0, 1.0) \
-  X(anderson, i, 0.0, 1.0) X(anderson_mem, i, 2.0, 5.0)
+  X(anderson, i, 0.0, 1.0) X(anderson_mem, i, 2.0, 5.0) X(autotune, i, 0.0, 1.0)
 
 int pdnqp_set_param(pdnqp_t *h, const char *name, double value) {
   if (!h || !name) return fail(h, PDNQP_ERR_ARG, "NULL handle or name");
@@ -558,6 +605,10 @@ int pdnqp_get_param(const pdnqp_t *h, const char *name, double *value) {
   }
   if (s == "create_setup_seconds") {
     *value = h->t_setup;
+    return 0;
+  }
+  if (s == "lanes_rows" || s == "lanes_cols") {
+    *value = h->solver->tuned_g(s == "lanes_cols" ? 0 : 1);
     return 0;
   }
 #define X(nm, kind, lo, hi) \

@@ -60,6 +60,7 @@ struct Params {
   double eps_inf = 0.0;        // infeasibility tolerance on l_inf-normalised directions (0: 1e-5)
   int anderson = 1;            // Anderson acceleration of (lambda, z)
   int anderson_mem = 5;        // stored outer iterates m_A (2..5)
+  int autotune = 0;            // 1: time the lanes-per-row choices of the graph form once, keep the fastest
 };
 
 struct Result {
@@ -86,6 +87,7 @@ class SolverBase {
   virtual int set_start(const double *x0, const double *lam0_int) = 0;
   virtual int debug_inner(Params &prm, int nck, const int64_t *ck, double *snap, std::string *err) = 0;
   virtual int replay(int which, int reps) = 0;
+  virtual int tuned_g(int which) const = 0;
   virtual double kernel_bytes(int which) const = 0;
   virtual double last_replay_ms() const = 0;
   virtual double gamma() const = 0;

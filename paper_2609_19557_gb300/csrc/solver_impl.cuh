@@ -696,6 +696,36 @@ class Solver : public SolverBase {
     });
   }
 
+  // Row-binning autotuner of the graph form: replays the row kernel and the
+  // column kernel (each captured as a graph of kTuneReps launches, on the
+  // state of the first inner solve) for every lanes-per-row choice, and makes
+  // the fastest the default of this handle.  Replays write trial buffers only
+  // and restore the device state.
+  int autotune_g() {
+    static constexpr int kTuneReps = 20;
+    const int cand[3] = {4, 8, 16};
+    const int gA = gA_, gN = gN_;
+    double best[2] = {INFINITY, INFINITY};
+    int pick[2] = {gA, gN};
+    for (int which = 0; which < 2; ++which)
+      for (int g : cand) {
+        if (which == 0) gN_ = g; else gA_ = g;
+        PDNQP_TRY(replay(which | 8, 1));  // first capture and launch (not timed)
+        PDNQP_TRY(replay(which | 8, kTuneReps));
+        if (last_replay_ms_ < best[which]) {
+          best[which] = last_replay_ms_;
+          pick[which] = g;
+        }
+        gA_ = gA;
+        gN_ = gN;
+      }
+    gN0_ = pick[0];
+    gA0_ = pick[1];
+    tuned_ = true;
+    return 0;
+  }
+  int tuned_g(int which) const override { return which == 0 ? gN0_ : gA0_; }
+
   // Lanes per CSR row: parameter override, else the mean-row-length choice of setup.
   void apply_g(const Params &prm) {
     gA_ = prm.g_rows > 0 ? prm.g_rows : gA0_;
@@ -1073,6 +1103,10 @@ class Solver : public SolverBase {
       PDNQP_CK(cudaMemcpyAsync(xprev_, x64_, sizeof(double) * n_, cudaMemcpyDeviceToDevice, s_));
       if (prm.anderson) PDNQP_TRY(aa_stage_u());
       PDNQP_TRY(inner_setup(prm, dta, dtr, std::min(prm.k_in, left), -1, 0));
+      if (prm.autotune && !tuned_ && (!prm.persistent || !coop_grid(prm.loop_blocks_per_sm))) {
+        PDNQP_TRY(autotune_g());
+        apply_g(prm);
+      }
       PDNQP_CK(cudaStreamSynchronize(s_));
       const double ts1 = now();
       t_setup += ts1 - ts0;
@@ -1497,6 +1531,7 @@ class Solver : public SolverBase {
   double gamma_pending_ = 0.0;
   long long trials_ = 0, accepted_ = 0, restarts_ = 0, launches_ = 0;
   bool ready_ = false, solved_once_ = false, has_x0_ = false, has_l0_ = false, own_stream_ = false;
+  bool tuned_ = false;
   std::vector<double> h_x0_, h_l0_;
   Result res_;
 };

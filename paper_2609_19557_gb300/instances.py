@@ -148,14 +148,23 @@ def _pack(Q, c, A, l_c, u_c, l_x, u_x, x0, **meta):
 
 
 def small_qp(seed: int = 0, n: int = 200, m: int = 100, q_offdiag_per_row: float = 2.0,
-             a_per_row: int = 4, neg_frac: float = 0.3, eq_frac: float = 0.2) -> dict:
+             a_per_row: int = 4, neg_frac: float = 0.3, eq_frac: float = 0.2, shift: float = None) -> dict:
     """n=200, m=100 nonconvex QP with box [0,1]; ~30% negative eigenvalues of Q."""
     rng = _rng(seed, WORKLOAD_CODES["small"])
     k = int(round(q_offdiag_per_row * n))
     r = rng.integers(0, n, size=k)
     cc = rng.integers(0, n, size=k)
     off = _sym_offdiag(n, r, cc, rng.standard_normal(k))
-    shift = _quantile_shift(off, neg_frac)
+    if shift is not None:
+        pass  # given by the caller (a batch shares one replica's quantile)
+    elif n <= 3000:
+        shift = _quantile_shift(off, neg_frac)
+    else:
+        # Large n: the quantile from an n = 3000 replica with the same density.
+        g = _rng(seed + 7919, WORKLOAD_CODES["small"])
+        kr = int(round(q_offdiag_per_row * 3000))
+        rep = _sym_offdiag(3000, g.integers(0, 3000, size=kr), g.integers(0, 3000, size=kr), g.standard_normal(kr))
+        shift = _quantile_shift(rep, neg_frac)
     Q = (off + shift * sp.identity(n, format="csr")).tocsr()
     A = _rows_with_lengths(rng, n, np.full(m, a_per_row))
     c = rng.standard_normal(n)
@@ -485,3 +494,26 @@ def svm_qp(seed: int = 101, n_target: int = 1_000_000) -> dict:
     A = sp.csr_matrix(y.reshape(1, N))
     return _pack(Q, -np.ones(N), A, np.zeros(1), np.zeros(1), np.zeros(N), np.full(N, Ua), np.zeros(N),
                  workload="svm", seed=seed, eta=eta, labels=y)
+
+
+def batched_set(seed: int = 0, count: int = 256, n_lo: int = 1000, n_hi: int = 100_000,
+                n_median: float = 4000.0, sigma: float = 0.8, clique_p: float = 0.01) -> list:
+    """A batch of independent problems of uneven sizes: n ~ lognormal (median
+    n_median, log-std sigma, clipped to [n_lo, n_hi]); even positions use the
+    small generator at that size with m = n / 2, odd positions Motzkin-Straus
+    QPs on G(n, clique_p).  Each problem has its own seed."""
+    rng = _rng(seed, WORKLOAD_CODES["batched"])
+    # One diagonal shift for the whole batch, from an n = 2000 replica of the
+    # small generator's off-diagonal density (30 % negative eigenvalues).
+    g = _rng(seed + 7919, WORKLOAD_CODES["batched"])
+    rep = _sym_offdiag(2000, g.integers(0, 2000, size=4000), g.integers(0, 2000, size=4000), g.standard_normal(4000))
+    shift = _quantile_shift(rep, 0.3)
+    ns = np.clip(np.exp(np.log(n_median) + sigma * rng.standard_normal(count)), n_lo, n_hi).astype(np.int64)
+    out = []
+    for k, n in enumerate(ns):
+        s = int(seed) * 100_003 + k
+        if k % 2 == 0:
+            out.append(small_qp(s, n=int(n), m=int(n) // 2, shift=shift))
+        else:
+            out.append(clique_qp(s, n=int(n), p=clique_p))
+    return out

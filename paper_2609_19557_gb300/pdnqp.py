@@ -27,7 +27,7 @@ EXPORTED = ["pdnqp_create", "pdnqp_create_ex", "pdnqp_destroy", "pdnqp_solve", "
             "pdnqp_replay_kernel", "pdnqp_kernel_bytes", "pdnqp_kkt_residuals", "pdnqp_kkt_last_error",
             "pdnqp_kkt_residuals_noalloc", "pdnqp_replay_last_ms", "pdnqp_mlp_param_count", "pdnqp_mlp_forward",
             "pdnqp_mlp_wmse", "pdnqp_mlp_backward", "pdnqp_mlp_adam", "pdnqp_mlp_to_bf16", "pdnqp_mlp_last_error",
-            "pdnqp_set_controller", "pdnqp_get_trace"]
+            "pdnqp_set_controller", "pdnqp_get_trace", "pdnqp_solve_batch"]
 
 
 class pdnqp_csr(C.Structure):
@@ -84,6 +84,7 @@ def load(path: str | None = None):
     L.pdnqp_destroy.argtypes = [vp]
     L.pdnqp_destroy.restype = None
     L.pdnqp_solve.argtypes = [vp, C.c_double, C.c_double]
+    L.pdnqp_solve_batch.argtypes = [C.POINTER(vp), C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int)]
     L.pdnqp_get.argtypes = [vp, vp, vp, C.POINTER(pdnqp_residuals)]
     L.pdnqp_set_start.argtypes = [vp, vp, vp]
     L.pdnqp_set_param.argtypes = [vp, C.c_char_p, C.c_double]
@@ -180,6 +181,15 @@ def pdnqp_destroy(h: Handle):
 
 def pdnqp_solve(h: Handle, eps_abs: float, eps_rel: float) -> int:
     return _check(h.ptr, load().pdnqp_solve(h.ptr, float(eps_abs), float(eps_rel)))
+
+
+def pdnqp_solve_batch(handles, eps_abs: float, eps_rel: float, threads: int = 0) -> list:
+    """Solves the problems of `handles` concurrently (pdnqp_solve_batch); returns their statuses."""
+    k = len(handles)
+    arr = (C.c_void_p * max(k, 1))(*[h.ptr for h in handles])
+    st = (C.c_int * max(k, 1))()
+    _check(None, load().pdnqp_solve_batch(arr, k, float(eps_abs), float(eps_rel), int(threads), st))
+    return list(st)[:k]
 
 
 def pdnqp_get(h: Handle):
