@@ -126,3 +126,13 @@ def test_clique_sparse_sampler():
     mu = p * n * (n - 1) / 2
     assert abs(e - mu) <= 5 * np.sqrt(mu)
     assert (inst["Q"] != -2.0 * G).nnz == 0
+
+
+def test_oracle_solves_flow_family(oracle):
+    """The oracle reaches rel-KKT 1e-4 on a small multistage-flow instance and
+    its own external KKT test accepts the point (the family is solvable by
+    the method as generated)."""
+    inst = I.flow_qp(101, n_target=1500)
+    x, y, info = oracle.solve(inst, eps_abs=1e-4, eps_rel=1e-4, time_limit=60)
+    assert info["status"] == 0
+    assert oracle.kkt_pass(inst, x, y, 1e-4, 1e-4)
