@@ -154,6 +154,17 @@ PDNQP_API int pdnqp_solve(pdnqp_t *h, double eps_abs, double eps_rel);
 PDNQP_API int pdnqp_solve_batch(pdnqp_t *const *hs, int count, double eps_abs, double eps_rel, int threads,
                                 int *status);
 
+/* Failure-detection self-test (no counterpart in the paper).  Makes one kind
+ * of bounded device wait of the persistent trial loop run out on purpose on
+ * the current device, without a fault: kind 0 = a grid barrier that one of
+ * its 4 blocks never reaches (the others poll the release up to their limit),
+ * kind 1 = a bulk-copy mbarrier that expects 16 bytes nothing sends.  On
+ * return *gave_up is 1 when every waiter gave up with a failure and set the
+ * fault flag, and *seconds (may be NULL) is the wall time of the launch
+ * (about a second or a few).  The context stays usable.  Returns 0,
+ * PDNQP_ERR_ARG or a CUDA error code. */
+PDNQP_API int pdnqp_selftest_wait(int kind, int *gave_up, double *seconds);
+
 /* Copies the result of the last pdnqp_solve: x (n entries, original
  * coordinates) and y (m entries, original row order, sign convention of Eq.
  * kkt-stationarity: 0 in Qx + c + A'y + N(x), so y <= 0 on rows active at

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpdnqp.so")
-SOURCES = ["api.cu", "solver_f64.cu", "solver_f32.cu", "kkt_check.cu", "mlp.cu"]
+SOURCES = ["api.cu", "solver_f64.cu", "solver_f32.cu", "kkt_check.cu", "mlp.cu", "selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-O2",
          "-Xcompiler", "-fvisibility=hidden"]

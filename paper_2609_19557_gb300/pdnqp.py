@@ -27,7 +27,8 @@ EXPORTED = ["pdnqp_create", "pdnqp_create_ex", "pdnqp_destroy", "pdnqp_solve", "
             "pdnqp_replay_kernel", "pdnqp_kernel_bytes", "pdnqp_kkt_residuals", "pdnqp_kkt_last_error",
             "pdnqp_kkt_residuals_noalloc", "pdnqp_replay_last_ms", "pdnqp_mlp_param_count", "pdnqp_mlp_forward",
             "pdnqp_mlp_wmse", "pdnqp_mlp_backward", "pdnqp_mlp_adam", "pdnqp_mlp_to_bf16", "pdnqp_mlp_last_error",
-            "pdnqp_set_controller", "pdnqp_get_trace", "pdnqp_solve_batch"]
+            "pdnqp_set_controller", "pdnqp_get_trace", "pdnqp_solve_batch",
+            "pdnqp_selftest_wait"]
 
 
 class pdnqp_csr(C.Structure):
@@ -84,6 +85,7 @@ def load(path: str | None = None):
     L.pdnqp_destroy.argtypes = [vp]
     L.pdnqp_destroy.restype = None
     L.pdnqp_solve.argtypes = [vp, C.c_double, C.c_double]
+    L.pdnqp_selftest_wait.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]
     L.pdnqp_solve_batch.argtypes = [C.POINTER(vp), C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int)]
     L.pdnqp_get.argtypes = [vp, vp, vp, C.POINTER(pdnqp_residuals)]
     L.pdnqp_set_start.argtypes = [vp, vp, vp]
@@ -190,6 +192,14 @@ def pdnqp_solve_batch(handles, eps_abs: float, eps_rel: float, threads: int = 0)
     st = (C.c_int * max(k, 1))()
     _check(None, load().pdnqp_solve_batch(arr, k, float(eps_abs), float(eps_rel), int(threads), st))
     return list(st)[:k]
+
+
+def pdnqp_selftest_wait(kind: int):
+    """Runs one bounded device wait out on purpose (see include/pdnqp.h); returns (gave_up, seconds)."""
+    g = C.c_int(-1)
+    t = C.c_double(0.0)
+    _check(None, load().pdnqp_selftest_wait(int(kind), C.byref(g), C.byref(t)))
+    return g.value == 1, t.value
 
 
 def pdnqp_get(h: Handle):

@@ -51,3 +51,19 @@ def test_last_error_without_handle(lib_path):
     from paper_2609_19557_gb300 import pdnqp as P
     P.load(lib_path)
     assert isinstance(P.pdnqp_last_error(None), str)
+
+
+def test_host_side_argument_checks(lib_path):
+    """Calls rejected before any device work (no GPU needed): an empty batch,
+    a batch with a NULL or repeated handle, an unknown self-test kind."""
+    from paper_2609_19557_gb300 import pdnqp as P
+    P.load(lib_path)
+    L = P.load()
+    st = (ctypes.c_int * 2)()
+    assert L.pdnqp_solve_batch(None, 0, 1e-4, 1e-4, 0, None) == 0
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert L.pdnqp_solve_batch(arr, 2, 1e-4, 1e-4, 0, st) == -1
+    assert L.pdnqp_solve_batch(arr, 2, -1.0, 1e-4, 0, st) == -1
+    g, t = ctypes.c_int(0), ctypes.c_double(0.0)
+    assert L.pdnqp_selftest_wait(7, ctypes.byref(g), ctypes.byref(t)) == -1
+    assert L.pdnqp_selftest_wait(0, None, None) == -1
