@@ -34,9 +34,33 @@ F0, NF = 3, 16          # feature columns in the trace
 A_RULE, A_TAKEN = 19, 21  # the rules' action (19, 20) and the action taken (21, 22)
 
 
-def make_instance(seed: int, n: int) -> dict:
+def make_instance(seed: int, n: int, shift: float = None) -> dict:
     """The mid-size generator (power-law rows, free variables, equality rows) at n variables, m = n / 2."""
-    return I.mid_qp(seed, n=n, m=n // 2, replica_n=min(3000, n))
+    return I.mid_qp(seed, n=n, m=n // 2, replica_n=min(3000, n), shift=shift)
+
+
+def generate_batched(count, rng, n_min, n_max, *, eps, explore, time_limit, threads, chunk=64):
+    """Training trajectories solved concurrently (pdnqp_solve_batch), `chunk`
+    problems at a time; the instances share the diagonal shift of the first
+    (same density), which saves the replica eigen-decomposition per instance."""
+    shift = None
+    data = []
+    for c0 in range(0, count, chunk):
+        hs = []
+        for i in range(c0, min(count, c0 + chunk)):
+            n = int(rng.integers(n_min, n_max + 1))
+            inst = make_instance(10_000 + i, n, shift=shift)
+            shift = inst["shift"]
+            h = P.create_from_instance(inst, precision=32)
+            P.pdnqp_set_param(h, "time_limit", time_limit)
+            P.pdnqp_set_param(h, "ctrl_explore", explore)
+            P.pdnqp_set_param(h, "ctrl_seed", i)
+            hs.append(h)
+        P.pdnqp_solve_batch(hs, eps, eps, threads=threads)
+        for h in hs:
+            data += transitions(P.pdnqp_get_trace(h))
+            h.close()
+    return data
 
 
 def run(inst: dict, *, precision=32, eps=1e-4, controller=None, explore=0.0, seed=0, time_limit=60.0, stream=None):
@@ -122,6 +146,10 @@ def main():
     ap.add_argument("--time-limit", type=float, default=60.0)
     ap.add_argument("--out", default=None)
     ap.add_argument("--data", default=None, help="transitions file (.npz): loaded if present, else written")
+    ap.add_argument("--threads", type=int, default=0, help="solve the training trajectories concurrently")
+    ap.add_argument("--eval-n-min", type=int, default=None)
+    ap.add_argument("--eval-n-max", type=int, default=None)
+    ap.add_argument("--compare", default=None, help="weights (.npy) evaluated on the same instances too")
     a = ap.parse_args()
     P.load()
     rng = np.random.default_rng(np.random.SeedSequence([2024, 7]))
@@ -131,6 +159,12 @@ def main():
         feats, acts, scores = z["feats"], z["acts"], z["scores"]
         for _ in range(a.train):  # keep the evaluation sizes of a fresh run
             rng.integers(a.n_min, a.n_max + 1)
+    elif a.threads > 0:
+        data = generate_batched(a.train, rng, a.n_min, a.n_max, eps=a.eps, explore=a.explore,
+                                time_limit=a.time_limit, threads=a.threads)
+        feats, acts, scores = (np.array(v) for v in zip(*data))
+        if a.data:
+            np.savez(a.data, feats=feats, acts=acts, scores=scores)
     else:
         data = []
         for i in range(a.train):
@@ -145,14 +179,20 @@ def main():
     if a.out:
         np.save(a.out, theta)
     rows = []
+    e_lo = a.eval_n_min if a.eval_n_min else a.n_min
+    e_hi = a.eval_n_max if a.eval_n_max else a.n_max
     for j in range(a.eval):
-        n = int(rng.integers(a.n_min, a.n_max + 1))
+        n = int(rng.integers(e_lo, e_hi + 1))
         inst = make_instance(90_000 + j, n)
         base, _ = run(inst, eps=a.eps, time_limit=a.time_limit)
         ctrl, _ = run(inst, eps=a.eps, controller=theta, time_limit=a.time_limit)
+        if a.compare:
+            old, _ = run(inst, eps=a.eps, controller=np.load(a.compare).astype(np.float32), time_limit=a.time_limit)
         rows.append({"n": n, **{f"rule_{k}": base[k] for k in ("status", "outer", "inner", "seconds", "rel_kkt")},
                      **{f"mlp_{k}": ctrl[k] for k in ("status", "outer", "inner", "seconds", "rel_kkt",
-                                                      "ctrl_used", "ctrl_fallbacks")}})
+                                                      "ctrl_used", "ctrl_fallbacks")},
+                     **({f"old_{k}": old[k] for k in ("status", "outer", "inner", "seconds", "rel_kkt")}
+                        if a.compare else {})})
     print(json.dumps({"trajectories": a.train, "transitions": len(scores), "generation_s": gen_s,
                       "loss": hist, "eval": rows}, default=float))
 

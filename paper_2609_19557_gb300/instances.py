@@ -175,7 +175,7 @@ def small_qp(seed: int = 0, n: int = 200, m: int = 100, q_offdiag_per_row: float
 
 def mid_qp(seed: int = 0, n: int = 50_000, m: int = 25_000, q_mean: float = 8.0, a_mean: float = 6.0,
            max_row: int = 200, free_frac: float = 0.1, eq_frac: float = 0.3, neg_frac: float = 0.3,
-           replica_n: int = 3000) -> dict:
+           replica_n: int = 3000, shift: float = None) -> dict:
     """Power-law rows (max 200 nnz), 10% free variables, 30% equality rows."""
     rng = _rng(seed, WORKLOAD_CODES["mid"])
 
@@ -187,8 +187,9 @@ def mid_qp(seed: int = 0, n: int = 50_000, m: int = 25_000, q_mean: float = 8.0,
         return _sym_offdiag(nn, rows, cols, g.standard_normal(rows.size))
 
     off = q_off(n, rng)
-    rep = q_off(min(replica_n, n), _rng(seed + 7919, WORKLOAD_CODES["mid"]))
-    shift = _quantile_shift(rep, neg_frac)
+    if shift is None:  # else given by the caller (many instances of one density share it)
+        rep = q_off(min(replica_n, n), _rng(seed + 7919, WORKLOAD_CODES["mid"]))
+        shift = _quantile_shift(rep, neg_frac)
     Q = (off + shift * sp.identity(n, format="csr")).tocsr()
     lens = _power_law_lengths(rng, m, a_mean, 1, max_row)
     A = _rows_with_lengths(rng, n, lens)
