@@ -52,6 +52,9 @@ def parse():
                    help="batched form instead: solve this many problems of uneven sizes concurrently")
     p.add_argument("--batch-threads", type=int, default=16)
     p.add_argument("--batch-time-limit", type=float, default=5.0, help="seconds per problem")
+    p.add_argument("--solve-times", action="store_true",
+                   help="instead: end-to-end solve times of the GPU forms and the oracle on the n=200 and "
+                        "n=50,000 workloads")
     p.add_argument("--n", type=int, default=1_000_000)
     p.add_argument("--m", type=int, default=500_000)
     return p.parse_args()
@@ -423,9 +426,45 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
+def run_solve_times(args):
+    """Wall time of pdnqp_solve (FP64 and FP32-bulk, persistent loop) and of the
+    FP64 oracle (one host core, 300 s cap) to rel-KKT 1e-4 and 1e-6 on the
+    n=200 (m=100) and n=50,000 (m=25,000) workloads; every final point is
+    judged by the oracle's external KKT test."""
+    from oracle import oracle as O
+    from paper_2609_19557_gb300 import instances as I
+    from paper_2609_19557_gb300 import pdnqp as P
+    O.build()
+    P.load()
+    rows = []
+    for name, inst in (("n=200 m=100", I.small_qp(0)), ("n=50000 m=25000", I.mid_qp(0))):
+        for eps in (1e-4, 1e-6):
+            row = {"workload": name, "eps": eps}
+            for prec in (64, 32):
+                h = P.create_from_instance(inst, precision=prec)
+                P.pdnqp_set_param(h, "time_limit", 300.0)
+                t0 = time.perf_counter()
+                st = P.pdnqp_solve(h, eps, eps)
+                dt = time.perf_counter() - t0
+                x, y, r = P.pdnqp_get(h)
+                h.close()
+                row[f"gpu_fp{prec}"] = {"status": P.STATUS_NAMES[st], "seconds": dt, "outer": r["outer_iters"],
+                                        "inner": r["inner_iters"], "kkt_pass": bool(O.kkt_pass(inst, x, y, eps, eps))}
+            t0 = time.perf_counter()
+            x, y, info = O.solve(inst, eps_abs=eps, eps_rel=eps, time_limit=300.0)
+            dt = time.perf_counter() - t0
+            row["oracle"] = {"status": info["status_name"], "seconds": dt, "outer": info["outer_iters"],
+                             "inner": info["inner_iters"], "kkt_pass": bool(O.kkt_pass(inst, x, y, eps, eps))}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+    print(json.dumps({"leg": "solve_times", "cores": 1, "rows": len(rows)}), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.batch > 0 and a.impl != "reference":
+    if a.solve_times and a.impl != "reference":
+        run_solve_times(a)
+    elif a.batch > 0 and a.impl != "reference":
         run_batch(a)
     elif a.impl == "reference":
         run_reference(a)
