@@ -136,7 +136,15 @@ PDNQP_API void pdnqp_destroy(pdnqp_t *h);
  * eps_rel s_d (Eq. outer-termination), or a limit is hit.  Starts from the
  * point given by pdnqp_set_start (default x0 = 0 projected on the box,
  * multipliers 0).  Returns a PDNQP_* status (>= 0) or an error code (< 0).
- * Calling it again restarts from the start point. */
+ * Calling it again restarts from the start point.  In the FP32-bulk form a
+ * solve that ends in NUMERICAL_ERROR (FP32 rounding can stall the acceptance
+ * test near a tight tolerance) continues, with parameter escalate = 1 (the
+ * default), as a solve of the plain FP64 form from the same start point,
+ * with the time that is left (so its result is the FP64 form's); the FP64
+ * solver is built on first use from a host copy of the prepared problem that
+ * FP32-bulk handles keep.  pdnqp_get then
+ * reports the FP64 result, with the iteration counters and times of both
+ * phases added up, and pdnqp_get_param(h, "escalated") is 1. */
 PDNQP_API int pdnqp_solve(pdnqp_t *h, double eps_abs, double eps_rel);
 
 /* The batched form: solves `count` independent problems, each with its own
@@ -202,12 +210,13 @@ PDNQP_API int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0);
  * autotune (1: when the graph form runs and g_rows / g_cols are 0, the first
  * inner solve times the row and column kernels for 4, 8 and 16 lanes per row
  * and keeps the fastest for this handle; 0, the default: the mean-row-length
- * choice).
+ * choice), escalate (FP32-bulk handles: 1, the default, continues a solve
+ * that ends in NUMERICAL_ERROR in the FP64 form, see pdnqp_solve; 0 = off).
  * Read-only names for pdnqp_get_param: gamma, precision, ruiz_outer,
  * create_prepare_seconds and create_setup_seconds (wall time of
  * pdnqp_create's host preparation and device setup), lanes_rows and
  * lanes_cols (the lanes-per-row defaults in use: the setup's choice or the
- * autotuner's).
+ * autotuner's), escalated (1 when the last solve finished in the FP64 form).
  * Returns PDNQP_ERR_ARG for an unknown name or an out-of-range value. */
 PDNQP_API int pdnqp_set_param(pdnqp_t *h, const char *name, double value);
 PDNQP_API int pdnqp_get_param(const pdnqp_t *h, const char *name, double *value);

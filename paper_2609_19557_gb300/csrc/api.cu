@@ -9,6 +9,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <numeric>
 #include <mutex>
@@ -35,6 +36,13 @@ struct pdnqp {
   int precision = PDNQP_FP64;
   int64_t nnzq = 0;
   double t_prepare = 0.0, t_setup = 0.0;  // wall time of pdnqp_create's host preparation and device setup
+  // FP32-bulk handles keep the prepared host problem, from which an FP64
+  // solver is built the first time a solve has to continue in FP64.
+  std::unique_ptr<HostProblem> host;
+  SolverBase *solver64 = nullptr;
+  bool escalated = false;  // the last solve finished in the FP64 solver
+  Result r32;              // counters of that solve's FP32 phase
+  std::vector<double> start_x, start_l;  // the start point given by pdnqp_set_start (internal row order)
 };
 
 static thread_local std::string g_err;
@@ -423,6 +431,7 @@ int pdnqp_create_ex(pdnqp_t **out, const pdnqp_csr *Q, const double *c, const pd
     delete h;
     return rc;
   }
+  if (o.precision == PDNQP_FP32_BULK) h->host.reset(new (std::nothrow) HostProblem(std::move(P)));
   const auto t2 = std::chrono::steady_clock::now();
   h->t_prepare = std::chrono::duration<double>(t1 - t0).count();
   h->t_setup = std::chrono::duration<double>(t2 - t1).count();
@@ -439,6 +448,7 @@ void pdnqp_destroy(pdnqp_t *h) {
   if (!h) return;
   cudaSetDevice(h->device);
   delete h->solver;
+  delete h->solver64;
   delete h;
 }
 
@@ -446,9 +456,43 @@ int pdnqp_solve(pdnqp_t *h, double eps_abs, double eps_rel) {
   if (!h) return fail(nullptr, PDNQP_ERR_ARG, "handle is NULL");
   if (!(eps_abs >= 0) || !(eps_rel >= 0)) return fail(h, PDNQP_ERR_ARG, "tolerances must be >= 0");
   cudaSetDevice(h->device);
+  h->escalated = false;
   std::string msg;
+  const auto t0 = std::chrono::steady_clock::now();
   int rc = h->solver->solve(eps_abs, eps_rel, h->prm, &msg);
   if (rc < 0) return fail(h, rc, msg);
+  const double used = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (rc == PDNQP_NUMERICAL_ERROR && h->precision == PDNQP_FP32_BULK && h->prm.escalate && h->host &&
+      used < h->prm.time_limit) {
+    // FP32 rounding stalls the acceptance test near a tight tolerance: the
+    // solve continues in the plain FP64 form from the FP32 form's last point.
+    if (!h->solver64) {
+      h->solver64 = pdq::make_solver_f64(h->stream);
+      const int rs = h->solver64->setup(*h->host, h->prm, &msg);
+      if (rs < 0) {
+        delete h->solver64;
+        h->solver64 = nullptr;
+        return fail(h, rs, msg);
+      }
+    }
+    // The FP64 solve starts from the handle's start point, not from the FP32
+    // point: it then returns exactly what the plain FP64 form returns (on the
+    // n = 50,000 workload at 1e-6 a warm start from the FP32 point was also
+    // slower, as the penalties and steps start over).
+    Result r32;
+    const int rg = h->solver->get(nullptr, nullptr, &r32);
+    if (rg < 0) return fail(h, rg, "escalation: reading the FP32 counters failed");
+    const int rst = h->solver64->set_start(h->start_x.empty() ? nullptr : h->start_x.data(),
+                                           h->start_l.empty() ? nullptr : h->start_l.data());
+    if (rst < 0) return fail(h, rst, "escalation: set_start failed");
+    Params p64 = h->prm;
+    p64.time_limit = h->prm.time_limit - used;
+    p64.controller = 0;  // the network's weights belong to the FP32 solver
+    rc = h->solver64->solve(eps_abs, eps_rel, p64, &msg);
+    if (rc < 0) return fail(h, rc, msg);
+    h->escalated = true;
+    h->r32 = r32;
+  }
   return rc;
 }
 
@@ -504,7 +548,19 @@ int pdnqp_get(const pdnqp_t *h, double *x, double *y, pdnqp_residuals *r) {
   cudaSetDevice(h->device);
   Result R;
   std::vector<double> lam_int(y ? h->m : 0);
-  int rc = h->solver->get(x, y ? lam_int.data() : nullptr, &R);
+  SolverBase *sv = h->escalated ? h->solver64 : h->solver;
+  int rc = sv->get(x, y ? lam_int.data() : nullptr, &R);
+  if (rc >= 0 && h->escalated) {  // counters cover both phases of the solve
+    R.outer += h->r32.outer;
+    R.inner += h->r32.inner;
+    R.trials += h->r32.trials;
+    R.restarts += h->r32.restarts;
+    R.passes += h->r32.passes;
+    R.seconds += h->r32.seconds;
+    R.launches += h->r32.launches;
+    R.inner_seconds += h->r32.inner_seconds;
+    R.setup_seconds += h->r32.setup_seconds;
+  }
   if (rc < 0) return fail(const_cast<pdnqp_t *>(h), rc, "pdnqp_get: no solution yet or CUDA failure");
   if (y)
     for (int k = 0; k < h->m; ++k) y[h->perm[k]] = lam_int[k];
@@ -520,8 +576,8 @@ int pdnqp_get(const pdnqp_t *h, double *x, double *y, pdnqp_residuals *r) {
     r->restarts = R.restarts;
     r->kkt_passes = R.passes;
     r->solve_seconds = R.seconds;
-    r->gamma = h->solver->gamma();
-    r->lambda_min = h->solver->lambda_min();
+    r->gamma = sv->gamma();
+    r->lambda_min = sv->lambda_min();
     r->obj = R.obj;
     r->kernel_launches = R.launches;
     r->inner_seconds = R.inner_seconds;
@@ -549,7 +605,12 @@ int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0) {
   if (x0)
     for (int i = 0; i < h->n; ++i)
       if (!std::isfinite(x0[i])) return fail(h, PDNQP_ERR_BOUNDS, "x0 has a non-finite entry");
-  return h->solver->set_start(x0, y0 ? l0.data() : nullptr);
+  const int rc = h->solver->set_start(x0, y0 ? l0.data() : nullptr);
+  if (rc == 0) {
+    h->start_x.assign(x0 ? x0 : nullptr, x0 ? x0 + h->n : nullptr);
+    h->start_l = l0;
+  }
+  return rc;
 }
 
 #define PDNQP_PARAMS(X)                                                                           \
@@ -563,7 +624,7 @@ int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0) {
   X(g_rows, i, 0.0, 16.0) X(g_cols, i, 0.0, 16.0) X(iter_budget, ll, 1.0, 4e18) X(cond_graph, i, 0.0, 1.0) \
   X(persistent, i, 0.0, 1.0) X(loop_blocks_per_sm, i, 0.0, 32.0) X(controller, i, 0.0, 1.0)             \
   X(ctrl_explore, d, 0.0, 10.0) X(ctrl_seed, ll, 0.0, 9.2e18) X(eps_inf, d, 0.0, 1.0) \
-  X(anderson, i, 0.0, 1.0) X(anderson_mem, i, 2.0, 5.0) X(autotune, i, 0.0, 1.0)
+  X(anderson, i, 0.0, 1.0) X(anderson_mem, i, 2.0, 5.0) X(autotune, i, 0.0, 1.0) X(escalate, i, 0.0, 1.0)
 
 int pdnqp_set_param(pdnqp_t *h, const char *name, double value) {
   if (!h || !name) return fail(h, PDNQP_ERR_ARG, "NULL handle or name");
@@ -605,6 +666,10 @@ int pdnqp_get_param(const pdnqp_t *h, const char *name, double *value) {
   }
   if (s == "create_setup_seconds") {
     *value = h->t_setup;
+    return 0;
+  }
+  if (s == "escalated") {
+    *value = h->escalated ? 1.0 : 0.0;
     return 0;
   }
   if (s == "lanes_rows" || s == "lanes_cols") {

@@ -61,6 +61,7 @@ struct Params {
   int anderson = 1;            // Anderson acceleration of (lambda, z)
   int anderson_mem = 5;        // stored outer iterates m_A (2..5)
   int autotune = 0;            // 1: time the lanes-per-row choices of the graph form once, keep the fastest
+  int escalate = 1;            // FP32-bulk: continue in FP64 after a NUMERICAL_ERROR
 };
 
 struct Result {

@@ -63,3 +63,29 @@ def test_fp32_end_to_end_mid(P, oracle):
     assert st == P.PDNQP_SOLVED, (P.STATUS_NAMES[st], res)
     assert oracle.kkt_pass(inst, x, y, 1e-4, 1e-4)
     h.close()
+
+
+def test_fp32_tight_tolerance_escalates_to_fp64(oracle):
+    """n = 50,000 to rel-KKT 1e-6: the FP32-bulk form alone ends in
+    NUMERICAL_ERROR (FP32 rounding stalls the acceptance test); with the
+    default escalation the solve continues as an FP64 solve from the same
+    start point and the result passes the oracle's KKT test at 1e-6."""
+    from paper_2609_19557_gb300 import build as B
+    from paper_2609_19557_gb300 import pdnqp as P
+    B.build()
+    P.load()
+    inst = I.mid_qp(0)
+    h = P.create_from_instance(inst, precision=32)
+    P.pdnqp_set_param(h, "escalate", 0)
+    P.pdnqp_set_param(h, "time_limit", 120.0)
+    st0 = P.pdnqp_solve(h, 1e-6, 1e-6)
+    assert P.pdnqp_get_param(h, "escalated") == 0
+    P.pdnqp_set_param(h, "escalate", 1)
+    st = P.pdnqp_solve(h, 1e-6, 1e-6)
+    x, y, r = P.pdnqp_get(h)
+    esc = P.pdnqp_get_param(h, "escalated")
+    h.close()
+    assert P.STATUS_NAMES[st] == "SOLVED", (P.STATUS_NAMES[st0], r)
+    assert oracle.kkt_pass(inst, x, y, 1e-6, 1e-6)
+    if P.STATUS_NAMES[st0] == "NUMERICAL_ERROR":
+        assert esc == 1
