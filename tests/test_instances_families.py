@@ -136,3 +136,25 @@ def test_oracle_solves_flow_family(oracle):
     x, y, info = oracle.solve(inst, eps_abs=1e-4, eps_rel=1e-4, time_limit=60)
     assert info["status"] == 0
     assert oracle.kkt_pass(inst, x, y, 1e-4, 1e-4)
+
+
+def test_batched_set_structure():
+    """Sizes inside the clip range, even positions from the small generator
+    with m = n/2, odd positions Motzkin-Straus (one simplex row, Q = -2 A_G),
+    one diagonal shift for the whole small-generator half, deterministic."""
+    B = I.batched_set(3, count=6, n_lo=1000, n_hi=1500, n_median=1200, sigma=0.5)
+    B2 = I.batched_set(3, count=6, n_lo=1000, n_hi=1500, n_median=1200, sigma=0.5)
+    shifts = set()
+    for k, (b, b2) in enumerate(zip(B, B2)):
+        n = b["Q"].shape[0]
+        assert 1000 <= n <= 1500
+        assert (b["Q"] != b2["Q"]).nnz == 0 and np.array_equal(b["c"], b2["c"])
+        assert _symmetric_exact(b["Q"])
+        if k % 2 == 0:
+            assert b["workload"] == "small" and b["A"].shape == (n, n // 2)[::-1]
+            shifts.add(b["shift"])
+            assert _feasible(b, b["x0"], tol=1e-9)
+        else:
+            assert b["workload"] == "clique" and b["A"].shape == (1, n)
+            assert np.all(b["Q"].diagonal() == 0) and np.all(b["Q"].data == -2.0)
+    assert len(shifts) == 1
