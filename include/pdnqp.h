@@ -366,7 +366,7 @@ PDNQP_API const char *pdnqp_mlp_last_error(void);
  * rho_in_min) * sigmoid(a[0]) and the next inner solve's starting primal
  * weight omega * exp(clamp(a[1], -1, 1)) (a network with a zero last layer
  * reproduces the rules).  The paper's rules stay the fallback and
- * the judge: an outer iteration after one whose network proposal increased
+ * overrule the network: an outer iteration after one whose proposal increased
  * the relative KKT residual uses the rules (Eq. inner-tolerance-factor, the
  * carried primal weight); so do iterations without weights or with
  * controller = 0.  The parameter ctrl_explore > 0 adds Gaussian noise of that

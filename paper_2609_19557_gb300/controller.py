@@ -12,8 +12,8 @@ log10 of the relative KKT residual per log10 of the inner iterations the next
 inner solve needed), and the network regresses onto the deviations from the
 rules that were taken, with weights exp(beta * standardised score).  Feature
 standardisation is folded into the first layer, so the solver feeds raw
-features.  In the solver the paper's rules stay the fallback and the judge
-(pdnqp_set_controller).
+features.  In the solver the paper's rules stay the fallback and decide when
+a proposal is overruled (pdnqp_set_controller).
 
     python -m paper_2609_19557_gb300.controller --train 200 --eval 8 --out weights.npy
 """
