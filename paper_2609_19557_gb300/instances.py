@@ -498,11 +498,12 @@ def svm_qp(seed: int = 101, n_target: int = 1_000_000) -> dict:
 
 
 def batched_set(seed: int = 0, count: int = 256, n_lo: int = 1000, n_hi: int = 100_000,
-                n_median: float = 4000.0, sigma: float = 0.8, clique_p: float = 0.01) -> list:
+                n_median: float = 4000.0, sigma: float = 0.8, clique_p: float = 0.01, only=None) -> list:
     """A batch of independent problems of uneven sizes: n ~ lognormal (median
     n_median, log-std sigma, clipped to [n_lo, n_hi]); even positions use the
     small generator at that size with m = n / 2, odd positions Motzkin-Straus
-    QPs on G(n, clique_p).  Each problem has its own seed."""
+    QPs on G(n, clique_p).  Each problem has its own seed, so `only` (positions)
+    builds a subset identical to those positions of the whole batch."""
     rng = _rng(seed, WORKLOAD_CODES["batched"])
     # One diagonal shift for the whole batch, from an n = 2000 replica of the
     # small generator's off-diagonal density (30 % negative eigenvalues).
@@ -511,7 +512,10 @@ def batched_set(seed: int = 0, count: int = 256, n_lo: int = 1000, n_hi: int = 1
     shift = _quantile_shift(rep, 0.3)
     ns = np.clip(np.exp(np.log(n_median) + sigma * rng.standard_normal(count)), n_lo, n_hi).astype(np.int64)
     out = []
+    keep = set(range(count)) if only is None else set(int(k) for k in only)
     for k, n in enumerate(ns):
+        if k not in keep:
+            continue
         s = int(seed) * 100_003 + k
         if k % 2 == 0:
             out.append(small_qp(s, n=int(n), m=int(n) // 2, shift=shift))
