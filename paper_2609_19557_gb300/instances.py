@@ -247,6 +247,28 @@ def large_qp(seed: int = 0, n: int = 1_000_000, m: int = 500_000, a_per_row: int
     return _pack(Q, c, A, l_c, u_c, -np.ones(n), np.ones(n), x0, workload="large", seed=seed, shift=shift)
 
 
+def _sorted_distinct(v: np.ndarray) -> np.ndarray:
+    """Sorted distinct values (what np.unique returns; sort + neighbour test is faster for large v)."""
+    v = np.sort(v)
+    return v[np.concatenate(([True], v[1:] != v[:-1]))] if v.size else v
+
+
+def _sym_pattern_csr(n: int, i: np.ndarray, j: np.ndarray) -> sp.csr_matrix:
+    """0/1 symmetric CSR with sorted rows from distinct pairs i < j sorted by
+    (i, j), written directly (row r: its lower neighbours, then its upper ones)."""
+    k = i.size
+    cl = np.bincount(j, minlength=n)
+    cu = np.bincount(i, minlength=n)
+    indptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(cl + cu, out=indptr[1:])
+    indices = np.empty(2 * k, dtype=np.int32)
+    order = np.argsort(j, kind="stable")  # lower entries by row j, columns i ascending
+    jl, il = j[order], i[order]
+    indices[indptr[jl] + np.arange(k) - (np.cumsum(cl) - cl)[jl]] = il
+    indices[indptr[i] + cl[i] + np.arange(k) - (np.cumsum(cu) - cu)[i]] = j
+    return sp.csr_matrix((np.ones(2 * k), indices, indptr), shape=(n, n))
+
+
 def clique_qp(seed: int = 0, n: int = 60, p: float = 0.1) -> dict:
     """Motzkin-Straus QP on G(n, p): min -x'A_G x s.t. sum(x) = 1, x >= 0 (Q = -2 A_G)."""
     rng = _rng(seed, WORKLOAD_CODES["clique"])
@@ -259,14 +281,16 @@ def clique_qp(seed: int = 0, n: int = 60, p: float = 0.1) -> dict:
         # pairs i < j (the same distribution as the pairwise draws above).
         npairs = n * (n - 1) // 2
         k = int(rng.binomial(npairs, p))
-        keys = np.unique(rng.integers(0, npairs, size=int(k * 1.1) + 16))
+        keys = _sorted_distinct(rng.integers(0, npairs, size=int(k * 1.1) + 16))
         while keys.size < k:
-            keys = np.unique(np.concatenate([keys, rng.integers(0, npairs, size=k - keys.size + 16)]))
-        keys = rng.permutation(keys)[:k]
+            keys = _sorted_distinct(np.concatenate([keys, rng.integers(0, npairs, size=k - keys.size + 16)]))
+        keys = np.sort(rng.permutation(keys)[:k])
         # Pair index -> (i, j), i < j, row-major over the upper triangle.
         i = (n - 2 - np.floor(np.sqrt(-8.0 * keys + 4.0 * n * (n - 1) - 7) / 2.0 - 0.5)).astype(np.int64)
         j = (keys + i + 1 - n * (n - 1) // 2 + (n - i) * ((n - i) - 1) // 2).astype(np.int64)
-        r, cc = i, j
+        AG = _sym_pattern_csr(n, i, j)
+        return _pack(-2.0 * AG, np.zeros(n), sp.csr_matrix(np.ones((1, n))), np.ones(1), np.ones(1), np.zeros(n),
+                     np.full(n, np.inf), np.full(n, 1.0 / n), workload="clique", seed=seed, graph=AG)
     G = sp.coo_matrix((np.ones(r.size), (r, cc)), shape=(n, n))
     AG = (G + G.T).tocsr()
     Q = (-2.0 * AG).tocsr()
