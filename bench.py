@@ -13,6 +13,14 @@ no flush is needed between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
        [--precision 32|64] [--budget B] [--ttk SECONDS]
+
+Other legs, each printing its own JSON line instead of the one above:
+  --batch K [--batch-threads T] [--batch-time-limit S]
+      the batched form: K independent problems of uneven sizes solved
+      concurrently (sharded by problem across ranks under torchrun);
+  --solve-times [--no-cpu]
+      end-to-end solve times of the GPU forms and the oracle on the n = 200
+      and n = 50,000 workloads, to rel-KKT 1e-4 and 1e-6.
 """
 from __future__ import annotations
 
