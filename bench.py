@@ -336,6 +336,21 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def host_cpu():
+    """The host's processor and core count (stated beside every CPU timing)."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware") and not model:
+                    model = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu": model or platform.processor() or "unknown", "arch": platform.machine()}
+
+
 def cpu_baseline(inst, first=2, last=6):
     """The oracle as it stands, single-threaded, on a bounded sample of the same
     workload: accepted inner iterations per second between two checkpoints of
@@ -346,7 +361,7 @@ def cpu_baseline(inst, first=2, last=6):
     if len(times) < 2:
         return None
     rate = (last - first) / (times[1] - times[0])
-    return {"value": rate, "unit": "iters/s", "cores": 1, "kind": "oracle",
+    return {"value": rate, "unit": "iters/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
             "sample": f"accepted inner iterations {first}..{last} of the first inner solve (setup {setup:.1f} s excluded)"}
 
 
@@ -369,7 +384,7 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": WORKLOAD, "n": args.n, "m": args.m,
                       "step": f"{per_step} accepted inner iteration(s) of the FP64 oracle"},
-           "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                             "sample": f"{args.steps} timed steps after {args.warmup} warm-up steps; setup "
                                       f"{setup:.1f} s excluded"},
            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -505,7 +520,7 @@ def run_solve_times(args):
                                  "inner": info["inner_iters"], "kkt_pass": bool(O.kkt_pass(inst, x, y, eps, eps))}
             rows.append(row)
             print(json.dumps(row), flush=True)
-    print(json.dumps({"leg": "solve_times", "cores": 1, "rows": len(rows)}), flush=True)
+    print(json.dumps({"leg": "solve_times", "cores": 1, "host": host_cpu(), "rows": len(rows)}), flush=True)
 
 
 if __name__ == "__main__":
