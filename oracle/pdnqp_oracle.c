@@ -202,6 +202,12 @@ static double clean_bound(double v) {
   return v;
 }
 static double dmax(double a, double b) { return a > b ? a : b; }
+/* Maxima of termination-test terms.  A residual term that is not finite (NaN
+ * or infinite data) counts as +inf, so a point with such entries never passes
+ * (a plain comparison-based maximum would drop a NaN).  A scale term that is
+ * not finite is left out: an infinite scale would excuse any residual. */
+static double rmax(double a, double b) { return isfinite(b) ? (a > b ? a : b) : INFINITY; }
+static double smax(double a, double b) { return (isfinite(b) && b > a) ? b : a; }
 static double dmin(double a, double b) { return a < b ? a : b; }
 
 /* The i-th output (i = 0, 1, ...) of the splitmix64 generator seeded with
@@ -836,27 +842,27 @@ static void outer_residuals(const sqp_t *S, const double *x, const double *lam, 
   for (int j = 0; j < m; ++j) {
     double v = ax[j], lo = S->lc[j], hi = S->uc[j];
     double viol = v < lo ? lo - v : (v > hi ? v - hi : 0.0);
-    a.rp = dmax(a.rp, viol);
-    a.sp = dmax(a.sp, fabs(v));
-    if (isfinite(lo)) a.sp = dmax(a.sp, fabs(lo));
-    if (isfinite(hi)) a.sp = dmax(a.sp, fabs(hi));
+    a.rp = rmax(a.rp, viol);
+    a.sp = smax(a.sp, fabs(v));
+    if (isfinite(lo)) a.sp = smax(a.sp, fabs(lo));
+    if (isfinite(hi)) a.sp = smax(a.sp, fabs(hi));
     double d = S->Dc[j];
-    b.rp = dmax(b.rp, viol / d);
-    b.sp = dmax(b.sp, fabs(v) / d);
-    if (isfinite(lo)) b.sp = dmax(b.sp, fabs(lo) / d);
-    if (isfinite(hi)) b.sp = dmax(b.sp, fabs(hi) / d);
+    b.rp = rmax(b.rp, viol / d);
+    b.sp = smax(b.sp, fabs(v) / d);
+    if (isfinite(lo)) b.sp = smax(b.sp, fabs(lo) / d);
+    if (isfinite(hi)) b.sp = smax(b.sp, fabs(hi) / d);
   }
   for (int i = 0; i < n; ++i) {
     double gsc = qx[i] + S->c[i] + atl[i];
-    a.rd = dmax(a.rd, fabs(x[i] - proj(x[i] - gsc, S->lx[i], S->ux[i])));
-    a.sd = dmax(a.sd, dmax(fabs(qx[i]), dmax(fabs(S->c[i]), fabs(atl[i]))));
+    a.rd = rmax(a.rd, fabs(x[i] - proj(x[i] - gsc, S->lx[i], S->ux[i])));
+    a.sd = smax(a.sd, smax(smax(fabs(qx[i]), fabs(S->c[i])), fabs(atl[i])));
     double f = 1.0 / (S->cs * S->Dx[i]);
     double xo = S->Dx[i] * x[i];
     double lo = S->lx[i] * S->Dx[i], hi = S->ux[i] * S->Dx[i];
     double go = gsc * f;
-    b.rd = dmax(b.rd, fabs(xo - proj(xo - go, lo, hi)));
-    b.rp = dmax(b.rp, xo < lo ? lo - xo : (xo > hi ? xo - hi : 0.0));
-    b.sd = dmax(b.sd, dmax(fabs(qx[i] * f), dmax(fabs(S->c[i] * f), fabs(atl[i] * f))));
+    b.rd = rmax(b.rd, fabs(xo - proj(xo - go, lo, hi)));
+    b.rp = rmax(b.rp, xo < lo ? lo - xo : (xo > hi ? xo - hi : 0.0));
+    b.sd = smax(b.sd, smax(smax(fabs(qx[i] * f), fabs(S->c[i] * f)), fabs(atl[i] * f)));
   }
   *sc = a; *un = b;
   free(ax); free(qx); free(atl);
@@ -1147,11 +1153,11 @@ int or_solve(const or_problem *P, const or_params *prm, double *x_out, double *y
     dta = dmax(dta * rho, prm->tol_floor * prm->eps_abs);
     dtr = dmax(dtr * rho, prm->tol_floor * prm->eps_rel);
     if (prm->verbose) {
-      double smax = 0.0;
-      for (int j = 0; j < m; ++j) smax = dmax(smax, T.sig[j]);
+      double sig_hi = 0.0;
+      for (int j = 0; j < m; ++j) sig_hi = dmax(sig_hi, T.sig[j]);
       fprintf(stderr, "k=%lld inner=%lld rp=%.3e rd=%.3e sp=%.3e sd=%.3e | un rp=%.3e rd=%.3e | dta=%.2e ratio=%.3f "
               "smax=%.2e eak=%.2e omega=%.3e\n", k, C.accepted, sc.rp, sc.rd, sc.sp, sc.sd, un.rp, un.rd, dta, ratio,
-              smax, eak, omega);
+              sig_hi, eak, omega);
     }
     /* Eq. center-update / center-tolerance-update. */
     if (sc.rp <= eak + erk * sc.sp) {
@@ -1326,17 +1332,17 @@ int or_kkt_check(const or_problem *P, const double *x, const double *lam, double
   for (int j = 0; j < m; ++j) {
     double lo = clean_bound(P->lc[j]), hi = clean_bound(P->uc[j]);
     double v = ax[j];
-    rp = dmax(rp, v < lo ? lo - v : (v > hi ? v - hi : 0.0));
-    sp = dmax(sp, fabs(v));
-    if (isfinite(lo)) sp = dmax(sp, fabs(lo));
-    if (isfinite(hi)) sp = dmax(sp, fabs(hi));
+    rp = rmax(rp, v < lo ? lo - v : (v > hi ? v - hi : 0.0));
+    sp = smax(sp, fabs(v));
+    if (isfinite(lo)) sp = smax(sp, fabs(lo));
+    if (isfinite(hi)) sp = smax(sp, fabs(hi));
   }
   for (int i = 0; i < n; ++i) {
     double lo = clean_bound(P->lx[i]), hi = clean_bound(P->ux[i]);
-    rp = dmax(rp, x[i] < lo ? lo - x[i] : (x[i] > hi ? x[i] - hi : 0.0));
+    rp = rmax(rp, x[i] < lo ? lo - x[i] : (x[i] > hi ? x[i] - hi : 0.0));
     double g = qx[i] + P->c[i] + atl[i];
-    rd = dmax(rd, fabs(x[i] - proj(x[i] - g, lo, hi)));
-    sd = dmax(sd, dmax(fabs(qx[i]), dmax(fabs(P->c[i]), fabs(atl[i]))));
+    rd = rmax(rd, fabs(x[i] - proj(x[i] - g, lo, hi)));
+    sd = smax(sd, smax(smax(fabs(qx[i]), fabs(P->c[i])), fabs(atl[i])));
   }
   out[0] = rp; out[1] = rd; out[2] = sp; out[3] = sd;
   free(ax); free(qx); free(atl);

@@ -280,6 +280,13 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar) {
 // warp w handles quantities w, w + nwarps, ...; lane l sums partials l, l + 32,
 // ... serially, then a fixed butterfly combines the 32 lane sums.  Every thread
 // of the block gets out[].  blockDim.x must be a multiple of 32.
+// Terms of the termination-test maxima (Eqs. outer-residuals / outer-scales).
+// fmax drops a NaN operand, so a residual term that is not finite counts as
+// +inf (a point with NaN or infinite entries never passes), and a scale term
+// that is not finite is left out (an infinite scale would excuse any residual).
+__device__ __forceinline__ double res_term(double v) { return isfinite(v) ? v : INFINITY; }
+__device__ __forceinline__ double scale_term(double v) { return isfinite(v) ? v : 0.0; }
+
 template <int NQ>
 __device__ __forceinline__ void final_reduce(const double *part, int nb, const unsigned kind_mask, double (&out)[NQ]) {
   __shared__ double res[NQ];

@@ -321,13 +321,13 @@ __global__ void __launch_bounds__(kBlock) k_outer_rows(Dev<T> d, Mat<double> Ad,
         q[4] = fmax(q[4], fabs(r));
       }
       const double viol = ax < lo ? lo - ax : (ax > hi ? ax - hi : 0.0);
-      double spv = fabs(ax);
+      double spv = scale_term(fabs(ax));
       if (isfinite(lo)) spv = fmax(spv, fabs(lo));
       if (isfinite(hi)) spv = fmax(spv, fabs(hi));
-      q[0] = fmax(q[0], viol);
+      q[0] = fmax(q[0], res_term(viol));
       q[1] = fmax(q[1], spv);
       const double dc = Dc[j];
-      q[2] = fmax(q[2], viol / dc);
+      q[2] = fmax(q[2], res_term(viol / dc));
       q[3] = fmax(q[3], spv / dc);
     }
   }
@@ -359,16 +359,16 @@ __global__ void __launch_bounds__(kBlock) k_outer_cols(Dev<T> d, Mat<double> Hd,
       double p = xi - g;
       p = p < lo ? lo : p;
       p = p > hi ? hi : p;
-      q[5] = fmax(q[5], fabs(xi - p));
-      q[6] = fmax(q[6], fmax(fabs(qx), fmax(fabs(c[i]), fabs(atl))));
+      q[5] = fmax(q[5], res_term(fabs(xi - p)));
+      q[6] = fmax(q[6], fmax(scale_term(fabs(qx)), fmax(fabs(c[i]), scale_term(fabs(atl)))));
       const double f = 1.0 / (cs * Dx[i]);
       const double xo = Dx[i] * xi, loo = lo * Dx[i], hio = hi * Dx[i], go = g * f;
       double po = xo - go;
       po = po < loo ? loo : po;
       po = po > hio ? hio : po;
-      q[7] = fmax(q[7], fabs(xo - po));
-      q[2] = fmax(q[2], xo < loo ? loo - xo : (xo > hio ? xo - hio : 0.0));
-      q[8] = fmax(q[8], fmax(fabs(qx * f), fmax(fabs(c[i] * f), fabs(atl * f))));
+      q[7] = fmax(q[7], res_term(fabs(xo - po)));
+      q[2] = fmax(q[2], res_term(xo < loo ? loo - xo : (xo > hio ? xo - hio : 0.0)));
+      q[8] = fmax(q[8], fmax(scale_term(fabs(qx * f)), fmax(fabs(c[i] * f), scale_term(fabs(atl * f)))));
       q[9] = fmax(q[9], fabs(xi - z[i]));
       q[10] += xi * qx;
       q[11] += c[i] * xi;

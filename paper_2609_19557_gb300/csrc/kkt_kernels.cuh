@@ -23,8 +23,8 @@ __global__ void __launch_bounds__(kBlock) k_kkt_rows(int m, const int *__restric
     double ax = 0.0;
     for (int k = rp[j]; k < rp[j + 1]; ++k) ax += v[k] * x[ci[k]];
     const double lo = lc[j] <= -1e20 ? -INFINITY : lc[j], hi = uc[j] >= 1e20 ? INFINITY : uc[j];
-    rpv = fmax(rpv, ax < lo ? lo - ax : (ax > hi ? ax - hi : 0.0));
-    spv = fmax(spv, fabs(ax));
+    rpv = fmax(rpv, res_term(ax < lo ? lo - ax : (ax > hi ? ax - hi : 0.0)));
+    spv = fmax(spv, scale_term(fabs(ax)));
     if (isfinite(lo)) spv = fmax(spv, fabs(lo));
     if (isfinite(hi)) spv = fmax(spv, fabs(hi));
   }
@@ -46,12 +46,12 @@ __global__ void __launch_bounds__(kBlock) k_kkt_cols(int n, const int *__restric
       for (int k = trp[i]; k < trp[i + 1]; ++k) aty += tv[k] * y[tci[k]];
     const double lo = lx[i] <= -1e20 ? -INFINITY : lx[i], hi = ux[i] >= 1e20 ? INFINITY : ux[i];
     const double xi = x[i];
-    rpv = fmax(rpv, xi < lo ? lo - xi : (xi > hi ? xi - hi : 0.0));
+    rpv = fmax(rpv, res_term(xi < lo ? lo - xi : (xi > hi ? xi - hi : 0.0)));
     double p = xi - (qx + c[i] + aty);
     p = p < lo ? lo : p;
     p = p > hi ? hi : p;
-    rdv = fmax(rdv, fabs(xi - p));
-    sdv = fmax(sdv, fmax(fabs(qx), fmax(fabs(c[i]), fabs(aty))));
+    rdv = fmax(rdv, res_term(fabs(xi - p)));
+    sdv = fmax(sdv, fmax(scale_term(fabs(qx)), fmax(fabs(c[i]), scale_term(fabs(aty)))));
   }
   double q[3] = {rpv, rdv, sdv};
   block_reduce_store<3>(q, 7u, part + 2 * kMaxBlocks);

@@ -65,3 +65,34 @@ def test_kkt_residuals_rejects_bad_input(P):
     rc = P.load().pdnqp_kkt_residuals(ctypes.byref(prob), None, None, None, None)
     assert rc == -1
     assert P.load().pdnqp_kkt_last_error()
+
+
+@pytest.mark.parametrize("where", ["x_first", "x_mid", "x_last", "y_mid", "x_inf"])
+def test_kkt_residuals_reject_nonfinite_point(P, oracle, where):
+    """A point with one NaN (or infinite) entry never passes the external KKT test
+    (Sec. 4.1): the maxima of Eqs. outer-residuals must not drop it, in either entry
+    point, and the oracle's checker agrees."""
+    import torch
+    inst = I.small_qp(2)
+    h = P.create_from_instance(inst)
+    assert P.pdnqp_solve(h, 1e-6, 1e-6) == P.PDNQP_SOLVED
+    x, y, _ = P.pdnqp_get(h)
+    h.close()
+    assert oracle.kkt_pass(inst, x, y, 1e-6, 1e-6)
+    x, y = x.copy(), y.copy()
+    pos = {"x_first": 0, "x_mid": x.size // 2, "x_last": x.size - 1}
+    if where == "y_mid":
+        y[y.size // 2] = np.nan
+    elif where == "x_inf":
+        x[x.size // 3] = np.inf
+    else:
+        x[pos[where]] = np.nan
+    assert not oracle.kkt_pass(inst, x, y, 1e-6, 1e-6)
+    prob = P.DeviceProblem(inst)
+    for fn in (P.pdnqp_kkt_residuals, P.pdnqp_kkt_residuals_noalloc):
+        out = torch.zeros(4, device="cuda", dtype=torch.float64)
+        fn(prob, torch.as_tensor(x, device="cuda"), torch.as_tensor(y, device="cuda"), out)
+        torch.cuda.synchronize()
+        rp, rd, sp, sd = out.cpu().numpy()
+        assert np.isfinite(sp) and np.isfinite(sd), (fn.__name__, sp, sd)
+        assert not (rp <= 1e-6 + 1e-6 * sp and rd <= 1e-6 + 1e-6 * sd), (fn.__name__, rp, rd)

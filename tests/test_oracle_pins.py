@@ -349,6 +349,27 @@ def test_kkt_checker_closed_forms(oracle):
     assert abs(rp2 - max(0.25, viol)) < 1e-12
 
 
+
+@pytest.mark.parametrize("where", ["x_first", "x_mid", "x_last", "y_first", "y_last", "x_inf"])
+def test_kkt_checker_rejects_nonfinite_point(oracle, where):
+    """External test of Sec. 4.1: a point with one NaN or infinite entry is not a KKT
+    point, wherever the entry sits (a maximum built from plain comparisons keeps a
+    NaN only when it comes last), while the scales stay finite."""
+    t = I.tiny_qp(0, n=5, m=3, eq_rows=1)
+    pts = BF.qp_kkt_points(t["Q"].toarray(), t["c"], t["A"].toarray(), t["l_c"], t["u_c"], t["l_x"], t["u_x"])
+    x, lam = (np.array(v, dtype=float) for v in pts[0])
+    assert oracle.kkt_pass(t, x, lam, 1e-8, 1e-8)
+    if where == "x_inf":
+        x[2] = np.inf
+    elif where.startswith("x"):
+        x[{"x_first": 0, "x_mid": 2, "x_last": 4}[where]] = np.nan
+    else:
+        lam[{"y_first": 0, "y_last": 2}[where]] = np.nan
+    rp, rd, sp_, sd = oracle.kkt_check(t, x, lam)
+    assert np.isfinite(sp_) and np.isfinite(sd)
+    assert rp == np.inf or rd == np.inf
+    assert not oracle.kkt_pass(t, x, lam, 1e-4, 1e-4)
+
 def test_end_to_end_small_workload(oracle):
     """n = 200, m = 100 workload: relative KKT 1e-4 reached and verified externally."""
     inst = I.small_qp(0)
