@@ -23,6 +23,8 @@ _lock = threading.Lock()
 _lib = None
 
 SNAP_SCALARS = 8
+CHK_COLS = 14
+OTR_COLS = 24
 STATUS = {0: "SOLVED", 1: "PRIMAL_INFEASIBLE", 2: "DUAL_INFEASIBLE", 3: "ITER_LIMIT", 4: "TIME_LIMIT",
           5: "NUMERICAL_ERROR"}
 
@@ -92,6 +94,9 @@ def lib():
             L.or_ruiz_outer.argtypes = [C.c_int, C.c_int] + [C.c_void_p] * 6 + [C.c_int, C.c_void_p, C.c_void_p]
             L.or_project.argtypes = [C.c_int] + [C.c_void_p] * 4
             L.or_debug_inner_timed.argtypes = [dp(_Problem), dp(_Params), C.c_int] + [C.c_void_p] * 4
+            L.or_debug_checks.argtypes = [dp(_Problem), dp(_Params), C.c_int, C.c_void_p, C.c_void_p]
+            L.or_solve_traced.argtypes = [dp(_Problem), dp(_Params), C.c_void_p, C.c_void_p, dp(_Result), C.c_int,
+                                          C.c_void_p, C.c_void_p, C.c_void_p]
             _lib = L
     return _lib
 
@@ -300,3 +305,60 @@ def anderson_step(U, G):
     out = np.zeros(U.shape[1])
     rc = lib().or_anderson_step(int(U.shape[0]), int(U.shape[1]), _ptr(U), _ptr(G), _ptr(out))
     return out if rc == 0 else None
+
+
+def debug_checks(inst: dict, max_checks: int, x0=None, **params):
+    """Trace of the periodic checks of the first inner solve (convergence ignored):
+    per check a dict with the scalars of the restart decision and the vectors w, y,
+    wbar, ybar, w_start, y_start (inner-unscaled) before it."""
+    P = Problem(inst, x0)
+    prm = default_params(**params)
+    info = setup_info(inst, x0, **params)
+    mI = P.m - info["mE"]
+    dw = P.n + mI + P.m
+    rows = np.zeros((max_checks, CHK_COLS))
+    vecs = np.zeros((max_checks, 3 * (dw + P.m)))
+    got = lib().or_debug_checks(P.ref(), C.byref(prm), int(max_checks), _ptr(rows), _ptr(vecs))
+    names = ["t_total", "t", "k_cur", "k_avg", "k_restart", "k_last", "use_avg", "restart", "omega",
+             "omega_after", "kappa", "kappa_after", "t_after", "k_restart_after"]
+    out = []
+    for r, v in zip(rows[:max(got, 0)], vecs[:max(got, 0)]):
+        d = dict(zip(names, r))
+        o = 0
+        for key, ln in (("w", dw), ("y", P.m), ("wbar", dw), ("ybar", P.m), ("wst", dw), ("yst", P.m)):
+            d[key] = v[o:o + ln]
+            o += ln
+        out.append(d)
+    return out, dict(info, dw=dw, mI=mI, status=got)
+
+
+def solve_traced(inst: dict, max_rows: int = 10000, x0=None, lam0=None, **params):
+    """solve() plus a per-outer-iteration trace of the outer rules (scaled internal
+    coordinates): list of dicts with the scalars and vectors of each iteration that
+    reached the tolerance update."""
+    P = Problem(inst, x0, lam0)
+    params.setdefault("time_limit", 120.0)
+    prm = default_params(**params)
+    n, m = P.n, P.m
+    x, y = np.zeros(n), np.zeros(m)
+    r = _Result()
+    rows = np.zeros((max_rows, OTR_COLS))
+    vecs = np.zeros((max_rows, 3 * n + 5 * m))
+    nr = C.c_int(0)
+    lib().or_solve_traced(P.ref(), C.byref(prm), _ptr(x), _ptr(y), C.byref(r), int(max_rows), _ptr(rows),
+                          _ptr(vecs), C.byref(nr))
+    info = {f[0]: getattr(r, f[0]) for f in _Result._fields_}
+    info["status_name"] = STATUS.get(info["status"], "?")
+    names = ["k", "primal_ok", "r_inf", "dx_inf", "sc_rp", "sc_rd", "sc_sp", "sc_sd", "un_rp", "un_rd", "un_sp",
+             "un_sd", "gamma", "ratio", "rho", "dta", "dtr", "dta_after", "dtr_after", "eak", "erk", "eak_after",
+             "erk_after", "moved"]
+    tr = []
+    for row, v in zip(rows[:nr.value], vecs[:nr.value]):
+        d = dict(zip(names, row))
+        o = 0
+        for key, ln in (("x", n), ("z", n), ("z_after", n), ("lam", m), ("sig", m), ("sig_after", m), ("r", m),
+                        ("r_prev", m)):
+            d[key] = v[o:o + ln]
+            o += ln
+        tr.append(d)
+    return x, y, info, tr

@@ -658,7 +658,14 @@ typedef struct {
   int next_ckpt;
   int ignore_convergence;
   double *times; /* optional: wall-clock seconds at each snapshot */
+  /* optional trace of the periodic checks (or_debug_checks): one row of
+   * CHK_COLS scalars and the vectors w, y, wbar, ybar, w_start, y_start
+   * (inner-unscaled coordinates) as they stand before the restart decision */
+  int chk_max, chk_n;
+  double *chk_rows, *chk_vecs;
 } dbg_t;
+
+#define CHK_COLS 14
 
 typedef struct {
   long long trials, accepted, restarts;
@@ -790,6 +797,18 @@ static int inner_solve(const sqp_t *S, const or_params *prm, const double *z, co
       int do_restart = kcand <= prm->beta_suff * k_restart ||
                        (kcand <= prm->beta_nec * k_restart && kcand > k_last) ||
                        (double)t >= prm->beta_art * (double)ttot;
+      double *crow = NULL;
+      if (D && D->chk_rows && D->chk_n < D->chk_max) {
+        crow = D->chk_rows + (size_t)D->chk_n * CHK_COLS;
+        crow[0] = (double)ttot; crow[1] = (double)t; crow[2] = kc; crow[3] = ka; crow[4] = k_restart;
+        crow[5] = k_last; crow[6] = use_avg; crow[7] = do_restart; crow[8] = omega; crow[10] = kappa;
+        double *cv = D->chk_vecs + (size_t)D->chk_n * 3 * (size_t)(dw + m);
+        for (int i = 0; i < dw; ++i) { cv[i] = I.ew[i] * w[i]; cv[dw + m + i] = I.ew[i] * wb[i];
+                                        cv[2 * (dw + m) + i] = I.ew[i] * wst[i]; }
+        for (int j = 0; j < m; ++j) { cv[dw + j] = I.dy[j] * yy[j]; cv[2 * dw + m + j] = I.dy[j] * yb[j];
+                                       cv[3 * dw + 2 * m + j] = I.dy[j] * yst[j]; }
+        D->chk_n++;
+      }
       k_last = kcand;
       if (do_restart) {
         if (use_avg) { memcpy(w, wb, sizeof(double) * dw); memcpy(yy, yb, sizeof(double) * m); }
@@ -807,6 +826,7 @@ static int inner_solve(const sqp_t *S, const or_params *prm, const double *z, co
         k_last = HUGE_VAL;
         C->restarts++;
       }
+      if (crow) { crow[9] = omega; crow[11] = kappa; crow[12] = (double)t; crow[13] = k_restart; }
     }
     if (D && D->next_ckpt < D->n_ckpt && ttot == D->ckpt[D->next_ckpt])
       take_snapshot(&I, D, w, yy, wb, yb, omega, kappa, t, ttot, C->trials, C->restarts, k_restart, k_last);
@@ -1079,7 +1099,42 @@ static void state_free(state_t *T) {
   free(T->x); free(T->lam); free(T->z); free(T->sig); free(T->rprev); free(T->yin);
 }
 
+/* Optional per-outer-iteration trace (or_solve_traced), for the pins of the
+ * outer rules: one row of OTR_COLS scalars per outer iteration that reached
+ * the tolerance update,
+ *   [0] k, [1] primal part of the termination test met, [2] ||r||_inf,
+ *   [3] ||x^{k+1} - z^k||_inf, [4..7] scaled r_p, r_d, s_p, s_d,
+ *   [8..11] the same on the original data, [12] gamma, [13] the ratio of Eq.
+ *   inner-tolerance-factor, [14] rho_in, [15..16] delta_a, delta_r before,
+ *   [17..18] after, [19..20] eps_a,k, eps_r,k before, [21..22] after,
+ *   [23] center moved
+ * and the vectors [x^{k+1} | z^k | z after the center update | lambda^{k+1} |
+ * sigma before | sigma after | r | r of the previous iteration] (n, n, n, m,
+ * m, m, m, m entries) in the scaled internal coordinates (rows E then I). */
+#define OTR_COLS 24
+typedef struct {
+  int max_rows, n_rows;
+  double *rows, *vecs;
+} otrace_t;
+
+static int solve_impl(const or_problem *P, const or_params *prm, double *x_out, double *y_out, or_result *res,
+                      otrace_t *TR);
+
 int or_solve(const or_problem *P, const or_params *prm, double *x_out, double *y_out, or_result *res) {
+  return solve_impl(P, prm, x_out, y_out, res, NULL);
+}
+
+/* or_solve with the outer trace; returns the status, rows written in *n_rows. */
+int or_solve_traced(const or_problem *P, const or_params *prm, double *x_out, double *y_out, or_result *res,
+                    int max_rows, double *rows, double *vecs, int *n_rows) {
+  otrace_t tr = {max_rows, 0, rows, vecs};
+  int st = solve_impl(P, prm, x_out, y_out, res, &tr);
+  *n_rows = tr.n_rows;
+  return st;
+}
+
+static int solve_impl(const or_problem *P, const or_params *prm, double *x_out, double *y_out, or_result *res,
+                      otrace_t *TR) {
   double t0 = now_seconds();
   state_t T;
   setup(P, prm, &T);
@@ -1139,6 +1194,22 @@ int or_solve(const or_problem *P, const or_params *prm, double *x_out, double *y
      * as long as the primal part of Eq. outer-termination is not met yet. */
     double rn = norm_inf(r, m);
     int primal_ok = un.rp <= prm->eps_abs + prm->eps_rel * un.sp && sc.rp <= prm->eps_abs + prm->eps_rel * sc.sp;
+    double *trow = NULL, *tvec = NULL;
+    if (TR && TR->n_rows < TR->max_rows) {
+      trow = TR->rows + (size_t)TR->n_rows * OTR_COLS;
+      tvec = TR->vecs + (size_t)TR->n_rows * (3 * (size_t)n + 5 * (size_t)m);
+      TR->n_rows++;
+      trow[0] = (double)k; trow[1] = primal_ok; trow[2] = rn;
+      trow[4] = sc.rp; trow[5] = sc.rd; trow[6] = sc.sp; trow[7] = sc.sd;
+      trow[8] = un.rp; trow[9] = un.rd; trow[10] = un.sp; trow[11] = un.sd; trow[12] = T.gamma;
+      trow[15] = dta; trow[16] = dtr; trow[19] = eak; trow[20] = erk;
+      memcpy(tvec, T.x, sizeof(double) * n);
+      memcpy(tvec + n, T.z, sizeof(double) * n);
+      memcpy(tvec + 3 * (size_t)n, T.lam, sizeof(double) * m);
+      memcpy(tvec + 3 * (size_t)n + m, T.sig, sizeof(double) * m);
+      memcpy(tvec + 3 * (size_t)n + 3 * (size_t)m, r, sizeof(double) * m);
+      memcpy(tvec + 3 * (size_t)n + 4 * (size_t)m, T.rprev, sizeof(double) * m);
+    }
     for (int j = 0; j < m; ++j) {
       int active = j < S->mE || T.lam[j] != 0.0;
       if (active && !primal_ok && fabs(r[j]) > prm->theta_sigma * fabs(T.rprev[j]) && rn > 0.0)
@@ -1152,6 +1223,10 @@ int or_solve(const or_problem *P, const or_params *prm, double *x_out, double *y
     double rho = prm->rho_in_max - (prm->rho_in_max - prm->rho_in_min) * ratio;
     dta = dmax(dta * rho, prm->tol_floor * prm->eps_abs);
     dtr = dmax(dtr * rho, prm->tol_floor * prm->eps_rel);
+    if (trow) {
+      trow[3] = dx; trow[13] = ratio; trow[14] = rho; trow[17] = dta; trow[18] = dtr;
+      memcpy(tvec + 3 * (size_t)n + 2 * (size_t)m, T.sig, sizeof(double) * m);
+    }
     if (prm->verbose) {
       double sig_hi = 0.0;
       for (int j = 0; j < m; ++j) sig_hi = dmax(sig_hi, T.sig[j]);
@@ -1160,10 +1235,15 @@ int or_solve(const or_problem *P, const or_params *prm, double *x_out, double *y
               sig_hi, eak, omega);
     }
     /* Eq. center-update / center-tolerance-update. */
-    if (sc.rp <= eak + erk * sc.sp) {
+    const int moved = sc.rp <= eak + erk * sc.sp;
+    if (moved) {
       memcpy(T.z, T.x, sizeof(double) * n);
       eak = dmax(eak * prm->rho_z, prm->eps_abs);
       erk = dmax(erk * prm->rho_z, prm->eps_rel);
+    }
+    if (trow) {
+      trow[21] = eak; trow[22] = erk; trow[23] = moved;
+      memcpy(tvec + 2 * (size_t)n, T.z, sizeof(double) * n);
     }
     /* Sec. "Anderson acceleration" (reading: active while the primal part of
      * the termination test holds on this and the previous outer iteration,
@@ -1234,6 +1314,32 @@ int or_debug_inner(const or_problem *P, const or_params *prm, int n_ckpt, const 
   if (gamma_out) *gamma_out = T.gamma;
   state_free(&T);
   return st == IN_NUMERICAL_ERROR ? -1 : D.next_ckpt;
+}
+
+/* Trace of the periodic checks of the first inner solve (convergence
+ * ignored) for the restart pins: the first max_checks checks, each one row of
+ * CHK_COLS scalars
+ *   [0] accepted iterations so far, [1] epoch length t, [2] KKT_w of the
+ *   current point, [3] of the average, [4] KKT_w at the last restart, [5] at
+ *   the previous check, [6] average chosen, [7] restart, [8] omega before,
+ *   [9] omega after, [10] kappa before, [11] kappa after, [12] t after,
+ *   [13] KKT_w at the last restart after the decision
+ * and the vectors [w | y | wbar | ybar | w_start | y_start] (dw and m
+ * entries each, inner-unscaled coordinates, rows E then I) before the
+ * decision.  Returns the number of rows written, or -1 on a numerical error. */
+int or_debug_checks(const or_problem *P, const or_params *prm, int max_checks, double *rows, double *vecs) {
+  state_t T;
+  setup(P, prm, &T);
+  double omega = 1.0;
+  ctr_t C = {0, 0, 0};
+  const long long stop = (long long)prm->k_chk * max_checks;
+  int dw = T.S.n + T.S.mI + T.S.m;
+  double *snap = dvec(2 * (size_t)(dw + T.S.m) + SNAP_SCALARS);
+  dbg_t D = {1, &stop, snap, 0, 1, NULL, max_checks, 0, rows, vecs};
+  int st = inner_solve(&T.S, prm, T.z, T.lam, T.sig, T.gamma, 1.0, 1.0, T.x, T.yin, &omega, &C, &D);
+  free(snap);
+  state_free(&T);
+  return st == IN_NUMERICAL_ERROR ? -1 : D.chk_n;
 }
 
 /* Scaling data of the setup, for tests: Dc (internal row order), Dx, perm, c_s, gamma, sigma0. */
