@@ -136,9 +136,15 @@ PDNQP_API void pdnqp_destroy(pdnqp_t *h);
  * eps_rel s_d (Eq. outer-termination), or a limit is hit.  Starts from the
  * point given by pdnqp_set_start (default x0 = 0 projected on the box,
  * multipliers 0).  Returns a PDNQP_* status (>= 0) or an error code (< 0).
- * Calling it again restarts from the start point.  In the FP32-bulk form a
- * solve that ends in NUMERICAL_ERROR (FP32 rounding can stall the acceptance
- * test near a tight tolerance) continues, with parameter escalate = 1 (the
+ * Calling it again restarts from the start point.  In the FP32-bulk form an
+ * inner solve that reaches the rejection limit (the FP32 products no longer
+ * resolve the step differences of Eq. adaptive-condition) does not end the
+ * solve: its last accepted point becomes the FP64 base of the next outer
+ * iteration, which re-warm-starts there with zero corrections (counted by
+ * pdnqp_get_param(h, "rebases")); two in a row without an accepted iteration
+ * between them, or non-finite sums, are a NUMERICAL_ERROR.  In the FP32-bulk
+ * form a solve that ends in NUMERICAL_ERROR continues, with parameter
+ * escalate = 1 (the
  * default), as a solve of the plain FP64 form from the same start point,
  * with the time that is left (so its result is the FP64 form's); the FP64
  * solver is built on first use from a host copy of the prepared problem that
@@ -216,7 +222,10 @@ PDNQP_API int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0);
  * create_prepare_seconds and create_setup_seconds (wall time of
  * pdnqp_create's host preparation and device setup), lanes_rows and
  * lanes_cols (the lanes-per-row defaults in use: the setup's choice or the
- * autotuner's), escalated (1 when the last solve finished in the FP64 form).
+ * autotuner's), escalated (1 when the last solve finished in the FP64 form),
+ * rebases (FP32-bulk: inner solves of the last solve that ended at the
+ * rejection limit and were continued from the last accepted point as a new
+ * FP64 base instead of ending the solve, see pdnqp_solve).
  * Returns PDNQP_ERR_ARG for an unknown name or an out-of-range value. */
 PDNQP_API int pdnqp_set_param(pdnqp_t *h, const char *name, double value);
 PDNQP_API int pdnqp_get_param(const pdnqp_t *h, const char *name, double *value);

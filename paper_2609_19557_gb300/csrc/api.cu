@@ -672,6 +672,12 @@ int pdnqp_get_param(const pdnqp_t *h, const char *name, double *value) {
     *value = h->escalated ? 1.0 : 0.0;
     return 0;
   }
+  if (s == "rebases") {
+    pdq::Result R;
+    (h->escalated ? h->solver64 : h->solver)->get(nullptr, nullptr, &R);
+    *value = (double)R.rebases;
+    return 0;
+  }
   if (s == "lanes_rows" || s == "lanes_cols") {
     *value = h->solver->tuned_g(s == "lanes_cols" ? 0 : 1);
     return 0;

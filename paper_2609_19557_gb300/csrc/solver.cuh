@@ -68,6 +68,7 @@ struct Result {
   int status = -1;
   double rp = 0, rd = 0, sp = 1, sd = 1, rel_kkt = 0;
   long long outer = 0, inner = 0, trials = 0, restarts = 0, passes = 0;
+  long long rebases = 0;  // FP32-bulk: inner solves re-based at the rejection limit
   double seconds = 0, obj = 0;
   long long launches = 0;
   double inner_seconds = 0, setup_seconds = 0;

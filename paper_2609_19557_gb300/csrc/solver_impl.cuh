@@ -872,7 +872,7 @@ class Solver : public SolverBase {
     }
     PDNQP_CK(cudaGetLastError());
     omega_ = 1.0;
-    trials_ = accepted_ = restarts_ = 0;
+    trials_ = accepted_ = restarts_ = rebases_ = 0;
     return 0;
   }
 
@@ -1124,6 +1124,20 @@ class Solver : public SolverBase {
       }
       PDNQP_TRY(finish_inner(S));
       if (S.status == ST_NUMERICAL_ERROR) {
+        // FP32-bulk: a run of rejections down to the limit means that the
+        // FP32 products H x_tr, A'y_tr (rounded to about 6e-8 of |H||dx|)
+        // no longer resolve the step differences of Eq. adaptive-condition.
+        // finish_inner has folded the last accepted point into the FP64 base,
+        // so the next outer iteration re-warm-starts there (as after the
+        // inner iteration limit) with zero corrections, which restores the
+        // FP32 resolution; a rebase that follows one without any accepted
+        // iteration in between is a true numerical error.  Non-finite sums
+        // (rej below the limit) are always a numerical error.
+        const bool floor = sizeof(T) == 4 && S.rej >= S.rej_limit && S.t_total > 0;
+        if (floor) {
+          ++rebases_;
+          continue;
+        }
         status = PDNQP_NUMERICAL_ERROR;
         ++k;
         break;
@@ -1278,6 +1292,7 @@ class Solver : public SolverBase {
     res_.inner = accepted_;
     res_.trials = trials_;
     res_.restarts = restarts_;
+    res_.rebases = rebases_;
     res_.passes = 3 * trials_ + 2 * (accepted_ / std::max(1, prm.k_chk));
     res_.seconds = seconds_since(t0);
     res_.launches = launches_;
@@ -1530,6 +1545,7 @@ class Solver : public SolverBase {
   double cs_ = 1.0, qnorm_ = 0.0, gamma_ = 1.0, lam_min_ = 0.0, sigma0_ = 1.0, omega_ = 1.0;
   double gamma_pending_ = 0.0;
   long long trials_ = 0, accepted_ = 0, restarts_ = 0, launches_ = 0;
+  long long rebases_ = 0;  // FP32-bulk inner solves ended at the rejection limit and re-based
   bool ready_ = false, solved_once_ = false, has_x0_ = false, has_l0_ = false, own_stream_ = false;
   bool tuned_ = false;
   std::vector<double> h_x0_, h_l0_;
