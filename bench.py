@@ -60,6 +60,8 @@ def parse():
                    help="batched form instead: solve this many problems of uneven sizes concurrently")
     p.add_argument("--batch-threads", type=int, default=16)
     p.add_argument("--batch-time-limit", type=float, default=5.0, help="seconds per problem")
+    p.add_argument("--batch-median", type=float, default=1e4, help="median n of the batch's log-normal sizes")
+    p.add_argument("--batch-sigma", type=float, default=1.0, help="log-std of the batch's sizes")
     p.add_argument("--solve-times", action="store_true",
                    help="instead: end-to-end solve times of the GPU forms and the oracle on the n=200 and "
                         "n=50,000 workloads")
@@ -295,13 +297,24 @@ def run_native(args):
         torch.cuda.synchronize()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
-        it64 = 0
+        it64, ls64, lt64 = 0, 0.0, 0
         for _ in range(max(1, args.steps // 2)):
             P.pdnqp_solve(h64, 1e-4, 1e-4)
-            it64 += P.pdnqp_get(h64)[2]["inner_iters"]
+            r64 = P.pdnqp_get(h64)[2]
+            it64 += r64["inner_iters"]
+            ls64 += r64["loop_seconds"]
+            lt64 += r64["loop_trials"]
         a1.record(stream)
         torch.cuda.synchronize()
         compare = {"fp64_iters_per_s": it64 / (a0.elapsed_time(a1) / 1e3)}
+        if lt64 > 0 and ls64 > 0:
+            # The plain FP64 form's trial loop against the same HBM roofline
+            # (one count per array per trial, 8-byte values).
+            b64 = trial_bytes(inst, 8)
+            ach64 = b64 * lt64 / ls64 / 1e9
+            compare["roofline"] = {"bound": "hbm", "achieved": ach64, "peak": peak, "unit": "GB/s",
+                                   "frac": ach64 / peak, "kernel": "k_trials<double>",
+                                   "algorithmic_bytes_per_trial": b64, "us_per_trial": 1e6 * ls64 / lt64}
         h64.close()
 
     ttk = None
@@ -348,7 +361,8 @@ def run_native(args):
         }
         if compare:
             out["vs_plain_fp64"] = {"fp64_iters_per_s": compare["fp64_iters_per_s"],
-                                    "speedup": value / ws / compare["fp64_iters_per_s"]}
+                                    "speedup": value / ws / compare["fp64_iters_per_s"],
+                                    "roofline": compare.get("roofline")}
         if ttk:
             out["time_to_1e-4"] = ttk
         print(json.dumps(out), flush=True)
@@ -436,10 +450,12 @@ def batch_totals(ws, wall, solved, inner, device):
 
 def run_batch(args):
     """Batched form: `args.batch` independent problems (sizes lognormal in
-    [1e3, 1e5], half from the small generator with m = n / 2, half
-    Motzkin-Straus on G(n, 0.01)) solved concurrently to rel-KKT 1e-4, each
-    with its own termination and a per-problem time limit; plus the first 8
-    problems solved one after another and as a batch, for the concurrency gain."""
+    [1e3, 1e5] with median --batch-median and log-std --batch-sigma; half from
+    the small generator with m = n / 2, half Motzkin-Straus on G(n, 0.01))
+    solved to rel-KKT 1e-4, each with its own termination and a per-problem
+    time limit, in the fused form (all inner iterations in one captured graph,
+    one launch per phase for the whole batch); plus the first 8 problems
+    solved one after another, in the fused form and in the thread-pool form."""
     import torch
     from paper_2609_19557_gb300 import instances as I
     from paper_2609_19557_gb300 import pdnqp as P
@@ -450,30 +466,46 @@ def run_batch(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     P.load()
     t = time.perf_counter()
-    insts = I.batched_set(0, count=args.batch, only=batch_shard(args.batch, ws, rank))
+    insts = I.batched_set(0, count=args.batch, only=batch_shard(args.batch, ws, rank),
+                          n_median=args.batch_median, sigma=args.batch_sigma)
     gen_s = time.perf_counter() - t
     t = time.perf_counter()
     hs = []
     for inst in insts:
         h = P.create_from_instance(inst, precision=args.precision)
         P.pdnqp_set_param(h, "time_limit", args.batch_time_limit)
-        P.pdnqp_set_param(h, "autotune", 1)
         hs.append(h)
     torch.cuda.synchronize()
     create_s = time.perf_counter() - t
 
-    def solve_all(sub, threads):
+    def solve_all(sub, fused, threads=16):
+        P.pdnqp_set_param(sub[0], "batch_fused", fused)
         t0 = time.perf_counter()
         sts = P.pdnqp_solve_batch(sub, 1e-4, 1e-4, threads=threads)
         return sts, time.perf_counter() - t0
 
     if ws > 1:
         torch.distributed.barrier()
-    sts, wall = solve_all(hs, args.batch_threads)
+    sts, wall = solve_all(hs, 1)
     res = [P.pdnqp_get(h)[2] for h in hs]
     names = [P.STATUS_NAMES[s] for s in sts]
     solved = names.count("SOLVED")
     inner = sum(r["inner_iters"] for r in res)
+    # HBM roofline of the batched graph: algorithmic bytes of every trial of
+    # every problem (one count per array per trial) over the device time of
+    # the graph launches (CUDA events on the batch's stream).
+    vb = 4 if args.precision == 32 else 8
+    trial_b = sum(r["trials"] * trial_bytes(inst, vb) for r, inst in zip(res, insts))
+    gsec = P.pdnqp_get_param(hs[0], "batch_graph_seconds")
+    peak, peak_src = measured_peaks()
+    roof = None
+    if gsec > 0:
+        ach = trial_b / gsec / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "kernel": "batched graph (kb_primal, kb_rows, kb_cols, kb_check_*), all problems",
+                "peak_source": peak_src, "graph_seconds": gsec,
+                "graph_launches": int(P.pdnqp_get_param(hs[0], "batch_graph_launches")),
+                "algorithmic_bytes": trial_b}
     wall, solved_all, inner_all = batch_totals(ws, wall, solved, inner, torch.device("cuda", local))
     if rank != 0:
         for h in hs:
@@ -486,23 +518,27 @@ def run_batch(args):
         P.pdnqp_set_param(h, "persistent", 0)
         P.pdnqp_solve(h, 1e-4, 1e-4)
     seq_s = time.perf_counter() - t0
-    _, bat_s = solve_all(sub, args.batch_threads)
+    _, fused_s = solve_all(sub, 1)
+    _, pool_s = solve_all(sub, 0, args.batch_threads)
     ns = [h.n for h in hs]
     out = {"metric": "batched solves to rel-KKT 1e-4", "value": solved_all / wall, "unit": "solved instances/s",
            "leg": "batched", "n_gpus": ws, "higher_is_better": True,
            "scaling": "strong (the batch is split by problem)" if ws > 1 else None,
            "dtype": "f32+f64" if args.precision == 32 else "f64",
            "data": "synthetic", "instances": args.batch, "solved": solved_all,
+           "instances_per_s": args.batch / wall,
            "statuses_rank0": {k: names.count(k) for k in sorted(set(names))},
            "wall_s": wall, "inner_iters_total": inner_all, "inner_iters_per_s": inner_all / wall,
-           "threads": args.batch_threads, "time_limit_per_problem_s": args.batch_time_limit,
+           "roofline": roof, "time_limit_per_problem_s": args.batch_time_limit,
            "generate_s": gen_s, "create_s": create_s,
-           "first8": {"sequential_s": seq_s, "batched_s": bat_s, "speedup": seq_s / bat_s},
-           "config": {"workload": f"{args.batch} independent nonconvex QPs: n lognormal (median 4000, log-std 0.8) clipped "
-                                  "to [1e3, 1e5]; half small generator (m = n/2), half Motzkin-Straus G(n, 0.01)",
+           "first8": {"sequential_s": seq_s, "fused_s": fused_s, "thread_pool_s": pool_s,
+                      "speedup_fused": seq_s / fused_s},
+           "config": {"workload": f"{args.batch} independent nonconvex QPs: n lognormal (median {args.batch_median:g}, "
+                                  f"log-std {args.batch_sigma:g}) clipped to [1e3, 1e5]; half small generator "
+                                  "(m = n/2), half Motzkin-Straus G(n, 0.01)",
                       "n_total": int(sum(ns)), "n_min": int(min(ns)), "n_max": int(max(ns)),
                       "n_scope": "rank 0 share" if ws > 1 else "whole batch",
-                      "form": "concurrent per-problem graph solves (pdnqp_solve_batch), autotuned lanes per row"}}
+                      "form": "fused: one captured graph, one launch per phase over all problems"}}
     for h in hs:
         h.close()
     print(json.dumps(out), flush=True)

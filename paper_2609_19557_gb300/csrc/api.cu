@@ -43,6 +43,10 @@ struct pdnqp {
   bool escalated = false;  // the last solve finished in the FP64 solver
   Result r32;              // counters of that solve's FP32 phase
   std::vector<double> start_x, start_l;  // the start point given by pdnqp_set_start (internal row order)
+  // Fused batched form: totals of the last pdnqp_solve_batch over this handle's precision group.
+  double batch_graph_seconds = 0.0;
+  long long batch_graph_launches = 0, batch_kernel_launches = 0;
+  int batch_size = 0;
 };
 
 static thread_local std::string g_err;
@@ -496,6 +500,102 @@ int pdnqp_solve(pdnqp_t *h, double eps_abs, double eps_rel) {
   return rc;
 }
 
+// The fused batched form: the problems of each precision get one scheduler
+// (pdq::BatchBase) that runs all their inner iterations in one launch per
+// phase of a captured CUDA graph; every problem's outer iteration runs on a
+// host thread of its own (pdnqp_solve, escalation included), which sleeps
+// while its inner solve is on the device.  Returns PDNQP_ERR_STATE without
+// solving anything when the handles are not all on one device.
+static int solve_batch_fused(pdnqp_t *const *hs, int count, double eps_abs, double eps_rel, int *status) {
+  const int dev = hs[0]->device;
+  for (int i = 0; i < count; ++i)
+    if (hs[i]->device != dev) return PDNQP_ERR_STATE;
+  cudaSetDevice(dev);
+  std::vector<int> keep(count), keep_tune(count);
+  for (int i = 0; i < count; ++i) {
+    keep[i] = hs[i]->prm.persistent;
+    keep_tune[i] = hs[i]->prm.autotune;
+    hs[i]->prm.persistent = 0;  // escalated FP64 solves run the graph form: no cooperative launch beside the batch
+    hs[i]->prm.autotune = 0;    // the per-handle tuner replays kernels on a running state: not beside the batch
+  }
+  struct Group {
+    std::vector<int> idx;
+    std::unique_ptr<pdq::BatchBase> batch;
+  };
+  Group groups[2];  // FP64, FP32-bulk
+  for (int i = 0; i < count; ++i) groups[hs[i]->precision == PDNQP_FP32_BULK ? 1 : 0].idx.push_back(i);
+  std::string err;
+  int rc = 0;
+  for (int g = 0; g < 2 && rc == 0; ++g) {
+    Group &G = groups[g];
+    if (G.idx.empty()) continue;
+    std::vector<SolverBase *> sv;
+    std::vector<int> gr, gc;
+    for (int i : G.idx) {
+      pdnqp_t *h = hs[i];
+      sv.push_back(h->solver);
+      gr.push_back(h->prm.g_rows > 0 ? h->prm.g_rows : h->solver->tuned_g(1));
+      gc.push_back(h->prm.g_cols > 0 ? h->prm.g_cols : h->solver->tuned_g(0));
+    }
+    const int chunk = hs[G.idx[0]]->prm.batch_chunk;
+    G.batch.reset(g ? pdq::make_batch_f32(sv, gr, gc, chunk, &err) : pdq::make_batch_f64(sv, gr, gc, chunk, &err));
+    if (!G.batch) rc = PDNQP_ERR_CUDA;
+  }
+  std::vector<int> rcs(count, 0);
+  std::vector<std::string> errs(count);
+  if (rc == 0) {
+    std::vector<std::thread> workers, schedulers;
+    int sched_rc[2] = {0, 0};
+    for (int g = 0; g < 2; ++g) {
+      Group &G = groups[g];
+      if (!G.batch) continue;
+      schedulers.emplace_back([&, g, dev] {
+        cudaSetDevice(dev);
+        sched_rc[g] = groups[g].batch->schedule();
+      });
+      for (int k = 0; k < (int)G.idx.size(); ++k)
+        workers.emplace_back([&, g, k] {
+          const int i = groups[g].idx[k];
+          rcs[i] = pdnqp_solve(hs[i], eps_abs, eps_rel);
+          if (rcs[i] < 0) errs[i] = g_err;
+          groups[g].batch->finished(k);
+        });
+    }
+    for (auto &t : workers) t.join();
+    for (auto &t : schedulers) t.join();
+    for (int g = 0; g < 2; ++g)
+      if (groups[g].batch)
+        for (int i : groups[g].idx) {
+          hs[i]->batch_graph_seconds = groups[g].batch->graph_seconds();
+          hs[i]->batch_graph_launches = groups[g].batch->graph_launches();
+          hs[i]->batch_kernel_launches = groups[g].batch->kernel_launches();
+          hs[i]->batch_size = (int)groups[g].idx.size();
+        }
+    for (int g = 0; g < 2; ++g)
+      if (sched_rc[g] < 0 && rc == 0) {
+        rc = sched_rc[g];
+        err = groups[g].batch->error();
+      }
+  }
+  for (int g = 0; g < 2; ++g) groups[g].batch.reset();
+  for (int i = 0; i < count; ++i) {
+    hs[i]->prm.persistent = keep[i];
+    hs[i]->prm.autotune = keep_tune[i];
+  }
+  if (rc < 0) return fail(nullptr, rc, "batch: " + err);
+  int worst = 0;
+  std::string first;
+  for (int i = 0; i < count; ++i) {
+    status[i] = rcs[i];
+    if (rcs[i] < 0 && worst == 0) {
+      worst = rcs[i];
+      first = errs[i];
+    }
+  }
+  if (worst < 0) return fail(nullptr, worst, "batch: " + first);
+  return 0;
+}
+
 int pdnqp_solve_batch(pdnqp_t *const *hs, int count, double eps_abs, double eps_rel, int threads, int *status) {
   if (count < 0 || (count > 0 && (!hs || !status))) return fail(nullptr, PDNQP_ERR_ARG, "bad batch arguments");
   if (!(eps_abs >= 0) || !(eps_rel >= 0)) return fail(nullptr, PDNQP_ERR_ARG, "tolerances must be >= 0");
@@ -505,6 +605,10 @@ int pdnqp_solve_batch(pdnqp_t *const *hs, int count, double eps_abs, double eps_
       if (hs[k] == hs[i]) return fail(nullptr, PDNQP_ERR_ARG, "batch handles must be distinct");
   }
   if (count == 0) return 0;
+  if (hs[0]->prm.batch_fused) {
+    const int rf = solve_batch_fused(hs, count, eps_abs, eps_rel, status);
+    if (rf != PDNQP_ERR_STATE) return rf;  // else: the batch does not fit the fused form
+  }
   // Largest problems first, so that the long solves start early.
   std::vector<int> order(count);
   std::iota(order.begin(), order.end(), 0);
@@ -624,7 +728,8 @@ int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0) {
   X(g_rows, i, 0.0, 16.0) X(g_cols, i, 0.0, 16.0) X(iter_budget, ll, 1.0, 4e18) X(cond_graph, i, 0.0, 1.0) \
   X(persistent, i, 0.0, 1.0) X(loop_blocks_per_sm, i, 0.0, 32.0) X(controller, i, 0.0, 1.0)             \
   X(ctrl_explore, d, 0.0, 10.0) X(ctrl_seed, ll, 0.0, 9.2e18) X(eps_inf, d, 0.0, 1.0) \
-  X(anderson, i, 0.0, 1.0) X(anderson_mem, i, 2.0, 5.0) X(autotune, i, 0.0, 1.0) X(escalate, i, 0.0, 1.0)
+  X(anderson, i, 0.0, 1.0) X(anderson_mem, i, 2.0, 5.0) X(autotune, i, 0.0, 1.0) X(escalate, i, 0.0, 1.0) \
+  X(batch_fused, i, 0.0, 1.0) X(batch_chunk, i, 1.0, 4096.0)
 
 int pdnqp_set_param(pdnqp_t *h, const char *name, double value) {
   if (!h || !name) return fail(h, PDNQP_ERR_ARG, "NULL handle or name");
@@ -670,6 +775,15 @@ int pdnqp_get_param(const pdnqp_t *h, const char *name, double *value) {
   }
   if (s == "escalated") {
     *value = h->escalated ? 1.0 : 0.0;
+    return 0;
+  }
+  if (s == "batch_graph_seconds") {
+    *value = h->batch_graph_seconds;
+    return 0;
+  }
+  if (s == "batch_graph_launches" || s == "batch_kernel_launches" || s == "batch_size") {
+    *value = (double)(s == "batch_size" ? h->batch_size
+                      : s == "batch_graph_launches" ? h->batch_graph_launches : h->batch_kernel_launches);
     return 0;
   }
   if (s == "rebases") {

@@ -20,6 +20,7 @@ enum InnerStatus : int {
   ST_NUMERICAL_ERROR = 3,
   ST_PAUSED = 4,
   ST_IDLE = 5,
+  ST_READY = 6,  // batched form: set up, waiting for the batch scheduler to let it run
 };
 
 // Scalar state of one inner solve.  Written by the host before the solve,
@@ -34,6 +35,7 @@ struct DevState {
   int restart_use_avg; // ... from the averaged candidate
   int ret_avg;         // converged candidate is the average
   int ignore_conv;     // debug: never stop on the inner termination test
+  int start_status;    // status the inner-solve setup ends in: ST_RUNNING, or ST_READY in the batched form
   long long t;         // accepted steps in the current epoch (N_p = N_d, Eq. pdqp-trial)
   long long t_total;   // accepted steps in this inner solve
   long long trials;    // all trials, all solves
@@ -79,6 +81,16 @@ __device__ __forceinline__ A group_max(A v) {
   return v;
 }
 
+// The blocks a kernel's work is spread over: the hardware grid, or, in the
+// batched form, the contiguous run of blocks of one launch that one problem
+// of the batch owns (block b of nb).  Reductions and grid-stride loops use
+// it instead of blockIdx / gridDim, so a problem sees the same partition
+// (and the same rounding) whether it runs alone or in a batch.
+struct GridCtx {
+  int b, nb;
+};
+__device__ __forceinline__ GridCtx hw_grid() { return GridCtx{(int)blockIdx.x, (int)gridDim.x}; }
+
 // Block reduction of NQ doubles; bit q of kind_mask: 0 sum, 1 max (all maxima
 // are of non-negative values).  Thread 0... of the block writes
 // part[q * kMaxBlocks + blockIdx.x].  Must be called by every thread of the
@@ -87,7 +99,9 @@ __device__ __forceinline__ A group_max(A v) {
 // shared memory and 8 threads per quantity sum 32 values each serially, then
 // one thread sums the 8.  Fixed order: deterministic for a fixed grid.
 template <int NQ>
-__device__ __forceinline__ void block_reduce_store(double (&v)[NQ], const unsigned kind_mask, double *part) {
+__device__ __forceinline__ void block_reduce_store(double (&v)[NQ], const unsigned kind_mask, double *part,
+                                                   int blk = -1) {
+  if (blk < 0) blk = blockIdx.x;
   constexpr int NW = kBlock / 32;
   constexpr int WIN = 4;  // quantities staged at a time (8 KB of shared memory)
   __shared__ double sm[WIN][kBlock];
@@ -119,7 +133,7 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NQ], const unsign
       const bool mx = (kind_mask >> q) & 1u;
       double a = s2[t][0];
       for (int c = 1; c < NW; ++c) a = mx ? fmax(a, s2[t][c]) : a + s2[t][c];
-      part[q * kMaxBlocks + blockIdx.x] = a;
+      part[q * kMaxBlocks + blk] = a;
     }
     __syncthreads();
   }
@@ -356,10 +370,10 @@ __device__ __forceinline__ Acc row_max(const int *__restrict__ rp, const int *__
 struct TileIter {
   int lane;
   long long first, step;
-  __device__ __forceinline__ TileIter() {
+  __device__ __forceinline__ TileIter(GridCtx g = hw_grid()) {
     lane = threadIdx.x & 31;
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long gw = ((long long)g.b * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)g.nb * blockDim.x) >> 5;
     first = gw * 32;
     step = nw * 32;
   }

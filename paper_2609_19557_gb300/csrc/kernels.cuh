@@ -115,6 +115,10 @@ struct SumT {
 #define PDNQP_GRID_STRIDE(i, N) \
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)(N); \
        i += (long long)gridDim.x * blockDim.x)
+// The same over the blocks of a GridCtx (one problem's share of a batched launch).
+#define PDNQP_VGRID_STRIDE(i, N, g) \
+  for (long long i = (long long)(g).b * blockDim.x + threadIdx.x; i < (long long)(N); \
+       i += (long long)(g).nb * blockDim.x)
 
 // The single-block kernels work on a shared-memory copy of the device state
 // (one coalesced load and store) instead of chains of dependent global
@@ -135,11 +139,12 @@ __global__ void k_loop_begin(DevState *st, long long chunk) { st->slot_left = ch
 // Last-block detection: after this block's partial sums are stored, returns
 // true in the single block that arrives last (its threads then see every
 // block's partials); that block resets the counter at the end of its work.
-__device__ __forceinline__ bool arrive_last(unsigned *ctr) {
+__device__ __forceinline__ bool arrive_last(unsigned *ctr, int nb = -1) {
   __shared__ bool last;
+  if (nb < 0) nb = gridDim.x;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(ctr, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) last = atomicAdd(ctr, 1u) == (unsigned)(nb - 1);
   __syncthreads();
   if (last) __threadfence();
   return last;
@@ -201,7 +206,7 @@ struct Pack {
 };
 
 template <typename T>
-__device__ __forceinline__ void primal_phase(const Dev<T> &d, const DevState *st) {
+__device__ __forceinline__ void primal_phase(const Dev<T> &d, const DevState *st, GridCtx g = hw_grid()) {
   const int cur = st->cur, a0 = st->acur, acc = st->accepted;
   const double t = (double)st->t;
   const T alpha = T(2.0 / (t + 2.0));
@@ -216,7 +221,7 @@ __device__ __forceinline__ void primal_phase(const Dev<T> &d, const DevState *st
   const long long nv = d.n / W;
   // W elements per thread and trip with 16-byte loads and stores; the same
   // arithmetic per element as the scalar tail below.
-  PDNQP_GRID_STRIDE(c, nv) {
+  PDNQP_VGRID_STRIDE(c, nv, g) {
     Pack<T> X, HX, HB, Q, AT, TA, L, U, XT;
     X.load(x, c);
     HX.load(Hx, c);
@@ -247,7 +252,7 @@ __device__ __forceinline__ void primal_phase(const Dev<T> &d, const DevState *st
     XT.store(xt, c);
   }
   // Tail (n mod W elements).
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long tid = (long long)g.b * blockDim.x + threadIdx.x;
   const long long i = nv * W + tid;
   if (i < d.n) {
     const T xi = x[i], hxi = Hx[i];
@@ -294,9 +299,9 @@ __device__ __forceinline__ double block_sum_fixed(double v) {
 }
 
 template <typename T>
-__device__ __forceinline__ void long_rows_partial(const Dev<T> &d, const T *xt) {
+__device__ __forceinline__ void long_rows_partial(const Dev<T> &d, const T *xt, GridCtx g = hw_grid()) {
   const long long L = d.lr_nnz;
-  const int nb = gridDim.x, b = blockIdx.x;
+  const int nb = g.nb, b = g.b;
   const long long e0 = lr_cut(L, b, nb), e1 = lr_cut(L, b + 1, nb);
   if (e0 >= e1) return;
   int s = 0;
@@ -396,7 +401,7 @@ __device__ void long_rows_finish(const Dev<T> &d, const DevState *st, int nb) {
 // dw^2 / tau and dy^2 / eta are accumulated with the stored inverses 1/tau0,
 // 1/eta0 and scaled once by omega / kappa and 1 / (kappa omega).
 template <typename T, int G>
-__device__ __forceinline__ void rows_phase(const Dev<T> &d, const DevState *st) {
+__device__ __forceinline__ void rows_phase(const Dev<T> &d, const DevState *st, GridCtx g = hw_grid()) {
   const int cur = st->cur, nx = 1 - cur, a0 = st->acur, acc = st->accepted;
   const double t = (double)st->t;
   const T alpha = T(2.0 / (t + 2.0)), oma = T(1) - alpha;
@@ -405,7 +410,7 @@ __device__ __forceinline__ void rows_phase(const Dev<T> &d, const DevState *st) 
   const T ap = T(st->alpha_acc), omap = T(1) - ap;
   const T *xt = d.x[nx];
   T Lt = T(0), Le = T(0), RH = T(0), RB = T(0);
-  TileIter ti;
+  TileIter ti(g);
   for (long long tile = ti.first; tile < d.m; tile += ti.step) {
     const long long j = tile + ti.lane;
     const bool valid = j < d.m && !(d.nlr && d.lr_flag[j]), ineq = j >= d.mE;
@@ -454,29 +459,35 @@ __device__ __forceinline__ void rows_phase(const Dev<T> &d, const DevState *st) 
     }
   }
   double v[4] = {double(Lt), double(Le), double(RH), double(RB)};
-  block_reduce_store<4>(v, 0u, d.part + P_TR_R * kMaxBlocks);
+  block_reduce_store<4>(v, 0u, d.part + P_TR_R * kMaxBlocks, g.b);
+}
+
+// Row pass of one trial over the blocks of g (graph and batched forms).
+template <typename T, int G>
+__device__ __forceinline__ void rows_trial_body(const Dev<T> &d, GridCtx g) {
+  if (d.st->status != ST_RUNNING) return;
+  if (d.nlr) long_rows_partial<T>(d, d.x[1 - d.st->cur], g);
+  rows_phase<T, G>(d, d.st, g);
+  if (d.nlr && arrive_last(d.ctr + 2, g.nb)) {
+    long_rows_finish<T>(d, d.st, g.nb);
+    if (threadIdx.x == 0) d.ctr[2] = 0u;
+  }
 }
 
 template <typename T, int G>
 __global__ void __launch_bounds__(kBlock) k_rows(Dev<T> d) {
-  if (d.st->status != ST_RUNNING) return;
-  if (d.nlr) long_rows_partial<T>(d, d.x[1 - d.st->cur]);
-  rows_phase<T, G>(d, d.st);
-  if (d.nlr && arrive_last(d.ctr + 2)) {
-    long_rows_finish<T>(d, d.st, gridDim.x);
-    if (threadIdx.x == 0) d.ctr[2] = 0u;
-  }
+  rows_trial_body<T, G>(d, hw_grid());
 }
 
 // Variable rows: (H x_tr)_i and (A' y_tr)_i (the products with Q and A^T),
 // plus the x terms of the acceptance sums.
 template <typename T, int GH, int GT>
-__device__ __forceinline__ void cols_phase(const Dev<T> &d, const DevState *st) {
+__device__ __forceinline__ void cols_phase(const Dev<T> &d, const DevState *st, GridCtx g = hw_grid()) {
   const int cur = st->cur, nx = 1 - cur;
   const T *xt = d.x[nx];
   const T *yt = d.y[nx];
   T Lt = T(0), RH = T(0), RB = T(0);
-  TileIter ti;
+  TileIter ti(g);
   for (long long tile = ti.first; tile < d.n; tile += ti.step) {
     const long long i = tile + ti.lane;
     // Row-local operands first: their loads overlap the SpMV chains.
@@ -504,20 +515,27 @@ __device__ __forceinline__ void cols_phase(const Dev<T> &d, const DevState *st) 
     }
   }
   double v[4] = {double(Lt), 0.0, double(RH), double(RB)};
-  block_reduce_store<4>(v, 0u, d.part + P_TR_C * kMaxBlocks);
+  block_reduce_store<4>(v, 0u, d.part + P_TR_C * kMaxBlocks, g.b);
 }
 
+// Column pass of one trial over the blocks of g, with the acceptance decision
+// in the problem's last block (graph and batched forms).
 template <typename T, int G, bool COND>
-__global__ void __launch_bounds__(kBlock) k_cols(Dev<T> d, int nb_r) {
+__device__ __forceinline__ void cols_trial_body(const Dev<T> &d, int nb_r, GridCtx g) {
   if (d.st->status != ST_RUNNING) {
     stop_loop<COND>(d.hw, d.hc);
     return;
   }
-  cols_phase<T, G, G>(d, d.st);
-  if (arrive_last(d.ctr)) {
-    decide_body<COND>(d.st, d.part, d.nlr ? d.lr_acc : nullptr, nb_r, gridDim.x, d.hw, d.hc);
+  cols_phase<T, G, G>(d, d.st, g);
+  if (arrive_last(d.ctr, g.nb)) {
+    decide_body<COND>(d.st, d.part, d.nlr ? d.lr_acc : nullptr, nb_r, g.nb, d.hw, d.hc);
     if (threadIdx.x == 0) d.ctr[0] = 0u;
   }
+}
+
+template <typename T, int G, bool COND>
+__global__ void __launch_bounds__(kBlock) k_cols(Dev<T> d, int nb_r) {
+  cols_trial_body<T, G, COND>(d, nb_r, hw_grid());
 }
 
 // ===========================================================================
@@ -1109,7 +1127,7 @@ __device__ __forceinline__ void row_cand(double *q, const RowIn &a) {
 }
 
 template <typename T, int G>
-__global__ void __launch_bounds__(kBlock) k_check_rows(Dev<T> d, int mode) {
+__device__ __forceinline__ void check_rows_body(const Dev<T> &d, int mode, GridCtx g) {
   const DevState *st = d.st;
   if (mode == 0 && !(st->status == ST_RUNNING && st->check_due)) return;
   // Averages of a pending acceptance are formed on the fly (and written for the
@@ -1121,7 +1139,7 @@ __global__ void __launch_bounds__(kBlock) k_check_rows(Dev<T> d, int mode) {
   double q[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) q[k] = 0.0;
-  TileIter ti;
+  TileIter ti(g);
   for (long long tile = ti.first; tile < d.m; tile += ti.step) {
     T axb = T(0);
     if (mode == 0)
@@ -1177,7 +1195,12 @@ __global__ void __launch_bounds__(kBlock) k_check_rows(Dev<T> d, int mode) {
       }
     }
   }
-  block_reduce_store<16>(q, CK_MAXMASK, d.part + P_CK_R * kMaxBlocks);
+  block_reduce_store<16>(q, CK_MAXMASK, d.part + P_CK_R * kMaxBlocks, g.b);
+}
+
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_check_rows(Dev<T> d, int mode) {
+  check_rows_body<T, G>(d, mode, hw_grid());
 }
 
 // Contributions of one variable (x block) to the 8 quantities of a candidate:
@@ -1200,7 +1223,7 @@ __device__ __forceinline__ void col_cand(double *q, double dx, double hdx, doubl
 }
 
 template <typename T, int G, bool COND>
-__global__ void __launch_bounds__(kBlock) k_check_cols(Dev<T> d, int mode, int nb_r) {
+__device__ __forceinline__ void check_cols_body(const Dev<T> &d, int mode, int nb_r, GridCtx g) {
   const DevState *st = d.st;
   if (mode == 0 && !(st->status == ST_RUNNING && st->check_due)) return;
   // y bar of a pending acceptance was materialised by k_check_rows.
@@ -1210,7 +1233,7 @@ __global__ void __launch_bounds__(kBlock) k_check_cols(Dev<T> d, int mode, int n
   double q[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) q[k] = 0.0;
-  TileIter ti;
+  TileIter ti(g);
   for (long long tile = ti.first; tile < d.n; tile += ti.step) {
     T atyb = T(0);
     if (mode == 0)
@@ -1235,14 +1258,19 @@ __global__ void __launch_bounds__(kBlock) k_check_cols(Dev<T> d, int mode, int n
       }
     }
   }
-  block_reduce_store<16>(q, CK_MAXMASK, d.part + P_CK_C * kMaxBlocks);
-  if (arrive_last(d.ctr + 1)) {
+  block_reduce_store<16>(q, CK_MAXMASK, d.part + P_CK_C * kMaxBlocks, g.b);
+  if (arrive_last(d.ctr + 1, g.nb)) {
     if (mode == 0)
-      check_final_body<COND>(d.st, d.part, nb_r, gridDim.x, d.hw);
+      check_final_body<COND>(d.st, d.part, nb_r, g.nb, d.hw);
     else
-      inner_begin_body(d.st, d.part, nb_r, gridDim.x);
+      inner_begin_body(d.st, d.part, nb_r, g.nb);
     if (threadIdx.x == 0) d.ctr[1] = 0u;
   }
+}
+
+template <typename T, int G, bool COND>
+__global__ void __launch_bounds__(kBlock) k_check_cols(Dev<T> d, int mode, int nb_r) {
+  check_cols_body<T, G, COND>(d, mode, nb_r, hw_grid());
 }
 
 // Decisions of the check (single block): inner termination of both candidates
@@ -1314,12 +1342,12 @@ __device__ void check_final_body(DevState *stg, const double *part, int nb_r, in
 // (with its cached products), then make it the epoch start and clear the
 // averages.  Idempotent, so a repeated launch is harmless.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_check_apply(Dev<T> d) {
+__device__ __forceinline__ void check_apply_body(const Dev<T> &d, GridCtx g) {
   const DevState *st = d.st;
   if (!st->restart_flag) return;
   const int cur = st->cur, ab = st->acur;
   const bool ua = st->restart_use_avg;
-  PDNQP_GRID_STRIDE(i, d.n) {
+  PDNQP_VGRID_STRIDE(i, d.n, g) {
     T x = d.x[cur][i], hx = d.Hx[cur][i];
     if (ua) {
       x = d.xbar[ab][i];
@@ -1332,7 +1360,7 @@ __global__ void __launch_bounds__(kBlock) k_check_apply(Dev<T> d) {
     d.xbar[ab][i] = x;
     d.Hxbar[ab][i] = hx;
   }
-  PDNQP_GRID_STRIDE(j, d.m) {
+  PDNQP_VGRID_STRIDE(j, d.m, g) {
     T y = d.y[cur][j], r = d.r[cur][j];
     if (ua) {
       y = d.ybar[ab][j];
@@ -1355,6 +1383,11 @@ __global__ void __launch_bounds__(kBlock) k_check_apply(Dev<T> d) {
       d.sbar[ab][j] = s;
     }
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_check_apply(Dev<T> d) {
+  check_apply_body<T>(d, hw_grid());
 }
 
 // ===========================================================================
@@ -1623,7 +1656,99 @@ __device__ void inner_begin_body(DevState *st, const double *part, int nb_r, int
   const double om = st->omega;
   st->k_restart = sqrt(om * (a[4] + b[4]) + (a[5] + b[5]) / om);
   st->k_last = INFINITY;
-  st->status = ST_RUNNING;
+  st->status = st->start_status;
+}
+
+
+// ===========================================================================
+// Batched form: the inner iterations of many problems in one launch per
+// phase.  Block k of a batched launch works for problem map[k].p as block
+// map[k].b of map[k].nb (the problem's own partition, the same as when it
+// runs alone, so its reductions and its iterates are bitwise those of its
+// solo graph-form solve); the problem's device pointers come from devs[p].
+// Every phase skips a problem whose status is not ST_RUNNING, so problems
+// that wait for their host outer iteration cost one state read per block.
+// ===========================================================================
+struct BatchBlk {
+  int p, b, nb;
+};
+
+// The problem's Dev copied to shared memory once per block (its pointers are
+// then read without a global-memory round trip per use).
+template <typename T>
+__device__ __forceinline__ const Dev<T> &batch_dev(const Dev<T> *devs, int p) {
+  __shared__ __align__(16) unsigned char buf[sizeof(Dev<T>)];
+  static_assert(sizeof(Dev<T>) % 4 == 0, "Dev must be a whole number of words");
+  const int *src = reinterpret_cast<const int *>(devs + p);
+  for (int i = threadIdx.x; i < (int)(sizeof(Dev<T>) / 4); i += blockDim.x) reinterpret_cast<int *>(buf)[i] = src[i];
+  __syncthreads();
+  return *reinterpret_cast<const Dev<T> *>(buf);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) kb_primal(const Dev<T> *devs, const BatchBlk *map) {
+  const BatchBlk e = map[blockIdx.x];
+  const Dev<T> &d = batch_dev(devs, e.p);
+  if (d.st->status != ST_RUNNING) return;
+  primal_phase<T>(d, d.st, GridCtx{e.b, e.nb});
+}
+
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) kb_rows(const Dev<T> *devs, const BatchBlk *map) {
+  const BatchBlk e = map[blockIdx.x];
+  rows_trial_body<T, G>(batch_dev(devs, e.p), GridCtx{e.b, e.nb});
+}
+
+// nb_rows[p]: blocks of problem p in the row launches (its row partials).
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) kb_cols(const Dev<T> *devs, const BatchBlk *map, const int *nb_rows) {
+  const BatchBlk e = map[blockIdx.x];
+  cols_trial_body<T, G, false>(batch_dev(devs, e.p), nb_rows[e.p], GridCtx{e.b, e.nb});
+}
+
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) kb_check_rows(const Dev<T> *devs, const BatchBlk *map) {
+  const BatchBlk e = map[blockIdx.x];
+  check_rows_body<T, G>(batch_dev(devs, e.p), 0, GridCtx{e.b, e.nb});
+}
+
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) kb_check_cols(const Dev<T> *devs, const BatchBlk *map,
+                                                        const int *nb_rows) {
+  const BatchBlk e = map[blockIdx.x];
+  check_cols_body<T, G, false>(batch_dev(devs, e.p), 0, nb_rows[e.p], GridCtx{e.b, e.nb});
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) kb_check_apply(const Dev<T> *devs, const BatchBlk *map) {
+  const BatchBlk e = map[blockIdx.x];
+  check_apply_body<T>(batch_dev(devs, e.p), GridCtx{e.b, e.nb});
+}
+
+// Scheduler edits between graph launches: problems in `go` that are set up
+// (ST_READY) start running; problems in `stop` that still run pause (their
+// time limit passed).
+template <typename T>
+__global__ void kb_control(const Dev<T> *devs, const int *go, int ngo, const int *stop, int nstop) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ngo + nstop; k += gridDim.x * blockDim.x) {
+    DevState *st = devs[k < ngo ? go[k] : stop[k - ngo]].st;
+    if (k < ngo) {
+      if (st->status == ST_READY) st->status = ST_RUNNING;
+    } else if (st->status == ST_RUNNING) {
+      st->status = ST_PAUSED;
+    }
+  }
+}
+
+// Copies every problem's device state into one array (one read-back per launch).
+template <typename T>
+__global__ void kb_gather_states(const Dev<T> *devs, int count, DevState *out) {
+  constexpr int W = (int)(sizeof(DevState) / 4);
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < (long long)count * W;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(k / W), w = (int)(k % W);
+    reinterpret_cast<int *>(out + p)[w] = __ldcg(reinterpret_cast<const int *>(devs[p].st) + w);
+  }
 }
 
 }  // namespace

@@ -62,6 +62,8 @@ struct Params {
   int anderson_mem = 5;        // stored outer iterates m_A (2..5)
   int autotune = 0;            // 1: time the lanes-per-row choices of the graph form once, keep the fastest
   int escalate = 1;            // FP32-bulk: continue in FP64 after a NUMERICAL_ERROR
+  int batch_fused = 1;         // pdnqp_solve_batch: 1 = one batched graph for all inner loops, 0 = thread pool
+  int batch_chunk = 16;        // trial slots per launch of the batched graph
 };
 
 struct Result {
@@ -103,5 +105,32 @@ class SolverBase {
 
 SolverBase *make_solver_f64(cudaStream_t s);
 SolverBase *make_solver_f32(cudaStream_t s);
+
+// Batched form (fused): the inner iterations of several solvers of one
+// precision run in one launch per phase of a captured CUDA graph, while
+// each problem's outer iteration (Algorithm 3) runs on its own host thread.
+// Built over solvers that have been set up; while it exists, their solves
+// hand every inner solve to it.
+class BatchBase {
+ public:
+  virtual ~BatchBase() {}
+  // Worker thread of problem idx: its pdnqp_solve has returned.
+  virtual void finished(int idx) = 0;
+  // Calling thread: launches the batched graph until every problem has
+  // finished; returns 0 or a negative code (the waiting solves then fail).
+  virtual int schedule() = 0;
+  virtual const std::string &error() const = 0;
+  // Graph launches and batched kernel launches so far.
+  virtual long long graph_launches() const = 0;
+  // Device time of the batched graph launches (CUDA events on the batch's stream).
+  virtual double graph_seconds() const = 0;
+  virtual long long kernel_launches() const = 0;
+};
+// g_rows[i] / g_cols[i]: lanes per row of problem i's row and column passes
+// (the values its solo graph form would use).
+BatchBase *make_batch_f64(const std::vector<SolverBase *> &sv, const std::vector<int> &g_rows,
+                          const std::vector<int> &g_cols, int chunk, std::string *err);
+BatchBase *make_batch_f32(const std::vector<SolverBase *> &sv, const std::vector<int> &g_rows,
+                          const std::vector<int> &g_cols, int chunk, std::string *err);
 
 }  // namespace pdq

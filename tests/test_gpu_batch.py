@@ -1,6 +1,8 @@
-"""Batched form: independent problems of uneven sizes solved concurrently
-(pdnqp_solve_batch), each with its own termination, and the row-binning
-autotuner of the graph form."""
+"""Batched form: independent problems of uneven sizes solved together
+(pdnqp_solve_batch), each with its own acceptance, restart and termination:
+the fused form (all inner iterations in one launch per phase of one captured
+CUDA graph) and the thread-pool form; and the row-binning autotuner of the
+graph form."""
 import numpy as np
 import pytest
 
@@ -14,8 +16,9 @@ def _batch():
     return I.batched_set(5, count=8, n_lo=1000, n_hi=3000, n_median=1800, sigma=0.4)
 
 
-def _make(P, inst, precision):
+def _make(P, inst, precision, fused=1):
     h = P.create_from_instance(inst, precision=precision)
+    P.pdnqp_set_param(h, "batch_fused", fused)
     # Bounded and deterministic (no time limit decides): 200 outer iterations
     # for the small generator, 20 for the slower Motzkin-Straus problems.
     P.pdnqp_set_param(h, "k_out", 200 if inst["workload"] == "small" else 20)
@@ -23,10 +26,13 @@ def _make(P, inst, precision):
     return h
 
 
+@pytest.mark.parametrize("fused", [1, 0])
 @pytest.mark.parametrize("precision", [64, 32])
-def test_batch_matches_sequential(P, oracle, precision):
-    """Each problem of the batch ends with the same status, iterates and
-    counts as when it is solved alone (the solves share nothing)."""
+def test_batch_matches_sequential(P, oracle, precision, fused):
+    """Each problem of the batch ends with the same status, bitwise the same
+    iterates and the same counts as when it is solved alone in the graph form
+    (the fused form gives each problem its solo block partition, so its
+    reductions round the same way)."""
     insts = _batch()
     seq = []
     for inst in insts:
@@ -35,7 +41,7 @@ def test_batch_matches_sequential(P, oracle, precision):
         x, y, r = P.pdnqp_get(h)
         seq.append((st, x, y, r["outer_iters"], r["inner_iters"]))
         h.close()
-    hs = [_make(P, inst, precision) for inst in insts]
+    hs = [_make(P, inst, precision, fused) for inst in insts]
     sts = P.pdnqp_solve_batch(hs, 1e-4, 1e-4, threads=4)
     solved = 0
     for k, (h, inst) in enumerate(zip(hs, insts)):
