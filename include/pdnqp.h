@@ -157,14 +157,24 @@ PDNQP_API int pdnqp_solve(pdnqp_t *h, double eps_abs, double eps_rel);
  * handle (distinct handles; each created on its own stream, which
  * pdnqp_create does when no stream is given), with per-problem termination
  * (Eq. outer-termination with eps_abs / eps_rel), restarts and limits.
- * `threads` host threads (0: min(count, 16)) take the problems largest
- * first and run pdnqp_solve on them concurrently, so the small inner solves
- * of different problems overlap on the GPU; every solve runs in the graph
- * form (the handle's "persistent" parameter is set to 0 for the call and
- * restored).  status[i] receives pdnqp_solve's return for hs[i]; the results
- * are read with pdnqp_get per handle.  Returns 0, or the first negative code
- * of a failed solve (the others still run to the end).  Blocks until all
- * solves have finished. */
+ * Fused form (parameter batch_fused = 1 on hs[0], the default; handles on one
+ * device): the inner iterations (Algorithm 4) of all problems of one
+ * precision run together in one captured CUDA graph of batch_chunk trial
+ * slots, one kernel launch per phase for the whole batch (per lanes-per-row
+ * group), with every problem's acceptance test, periodic check, restart and
+ * inner termination taken on the device; each problem's outer iteration
+ * (Algorithm 3, Sec. 3.4's CPU side) runs on a host thread of its own (one
+ * per problem; `threads` is not used), which sleeps while its inner solve is
+ * in the graph.  A problem keeps its solo block partition, so its results
+ * are bitwise those of its solo graph-form solve.  Thread-pool form
+ * (batch_fused = 0): `threads` host threads (0: min(count, 16)) run
+ * pdnqp_solve on the problems, largest first, so their graph-form inner
+ * solves overlap on the GPU.  In both forms every solve runs the graph form
+ * (the handles' "persistent" and "autotune" parameters are set to 0 for the
+ * call and restored).  status[i] receives pdnqp_solve's return for hs[i];
+ * the results are read with pdnqp_get per handle.  Returns 0, or the first
+ * negative code of a failed solve (the others still run to the end).  Blocks
+ * until all solves have finished. */
 PDNQP_API int pdnqp_solve_batch(pdnqp_t *const *hs, int count, double eps_abs, double eps_rel, int threads,
                                 int *status);
 
@@ -217,12 +227,19 @@ PDNQP_API int pdnqp_set_start(pdnqp_t *h, const double *x0, const double *y0);
  * inner solve times the row and column kernels for 4, 8 and 16 lanes per row
  * and keeps the fastest for this handle; 0, the default: the mean-row-length
  * choice), escalate (FP32-bulk handles: 1, the default, continues a solve
- * that ends in NUMERICAL_ERROR in the FP64 form, see pdnqp_solve; 0 = off).
+ * that ends in NUMERICAL_ERROR in the FP64 form, see pdnqp_solve; 0 = off),
+ * batch_fused and batch_chunk (read from the first handle of a
+ * pdnqp_solve_batch call: 1, the default, = the fused batched form, 0 = the
+ * thread-pool form; trial slots per launch of the batched graph, default 16).
  * Read-only names for pdnqp_get_param: gamma, precision, ruiz_outer,
  * create_prepare_seconds and create_setup_seconds (wall time of
  * pdnqp_create's host preparation and device setup), lanes_rows and
  * lanes_cols (the lanes-per-row defaults in use: the setup's choice or the
  * autotuner's), escalated (1 when the last solve finished in the FP64 form),
+ * batch_graph_seconds, batch_graph_launches, batch_kernel_launches and
+ * batch_size (the last fused pdnqp_solve_batch over this handle's precision
+ * group: device time of its graph launches, their number, the batched
+ * kernels they ran and the group's problem count),
  * rebases (FP32-bulk: inner solves of the last solve that ended at the
  * rejection limit and were continued from the last accepted point as a new
  * FP64 base instead of ending the solve, see pdnqp_solve).
@@ -317,8 +334,11 @@ PDNQP_API const char *pdnqp_kkt_last_error(void);
  *     kernels stride over rows with at most 1216 blocks); larger ones are
  *     rejected with PDNQP_ERR_ARG and a message.
  *   - Set-up: the first call on each device looks up the device address of
- *     that array (cudaGetSymbolAddress) with the device current; make that
- *     first call before any stream capture.
+ *     that array (cudaGetSymbolAddress) with the device current and keeps it
+ *     for the life of the process; make that first call before any stream
+ *     capture.  A cudaDeviceReset unloads the library's device code, so the
+ *     kept address is no longer valid afterwards: a process that resets a
+ *     device must not call this entry point on that device again.
  *   - All calls on a device share the array and it keeps the last call's
  *     contents (no clearing is needed: each call writes every entry it
  *     reads).  Calls that overlap on the GPU (other streams, other host

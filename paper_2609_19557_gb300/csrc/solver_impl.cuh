@@ -45,8 +45,24 @@ static int pick_g(long long nnz, long long rows) {
   return g;
 }
 
+// Where a solver in the batched form hands its inner solves (BatchRunner).
+struct BatchHook {
+  virtual ~BatchHook() {}
+  // Blocks until inner solve idx has left the running state; returns 1 when
+  // it was stopped at its time limit (deadline, steady-clock seconds), else 0.
+  virtual int run_inner(int idx, DevState *S, double deadline) = 0;
+};
+
+// Smallest relative inner tolerance of the FP32-bulk form: 8 units of FP32 roundoff (2^-24).
+constexpr double kFp32RelTolFloor = 8.0 * 5.9604644775390625e-8;
+
+template <typename T>
+class BatchRunner;
+
 template <typename T>
 class Solver : public SolverBase {
+  friend class BatchRunner<T>;
+
  public:
   explicit Solver(cudaStream_t s) : s_(s) {
     // Stream capture needs a non-default stream: make one when none is given.
@@ -910,6 +926,7 @@ class Solver : public SolverBase {
     S.restart_flag = 0;
     S.ret_avg = 0;
     S.ignore_conv = ignore;
+    S.start_status = batch_ ? ST_READY : ST_RUNNING;
     S.t = 0;
     S.t_total = 0;
     S.trials = trials_;
@@ -954,6 +971,16 @@ class Solver : public SolverBase {
 
   // Runs graph chunks until the device status leaves RUNNING.
   int run_until_stop(const Params &prm, DevState *S, double t0) {
+    if (batch_) {
+      PDNQP_CK(cudaStreamSynchronize(s_));  // the setup of this inner solve is complete
+      const int r = batch_->run_inner(batch_idx_, S, t0 + prm.time_limit);
+      if (r < 0) {
+        last_err_ = "batched form: the scheduler stopped";
+        return r;
+      }
+      *hst_ = *S;
+      return r;
+    }
     const int nbp = prm.persistent ? coop_grid(prm.loop_blocks_per_sm) : 0;
     if (nbp > 0) {
       // Persistent loop: batches of slots [trial loop, check rows, check cols
@@ -1248,6 +1275,12 @@ class Solver : public SolverBase {
       }
       dta = std::max(dta * rho, prm.tol_floor * ea);
       dtr = std::max(dtr * rho, prm.tol_floor * er);
+      // FP32-bulk: the inner residuals are formed from FP32 iterates and
+      // cached products, whose rounding is about 2^-24 of the terms that
+      // make up the scales of Eq. inner-scales; a relative inner tolerance
+      // below a few units of it cannot be certified (the inner solve would
+      // run to K_in on rounding noise), so delta_r stops at 8 units.
+      if (sizeof(T) == 4) dtr = std::max(dtr, kFp32RelTolFloor);
       // Eq. center-update / center-tolerance-update.
       if (rps <= eak + erk * sps) {
         PDNQP_CK(cudaMemcpyAsync(z_, x64_, sizeof(double) * n_, cudaMemcpyDeviceToDevice, s_));
@@ -1546,6 +1579,8 @@ class Solver : public SolverBase {
   double gamma_pending_ = 0.0;
   long long trials_ = 0, accepted_ = 0, restarts_ = 0, launches_ = 0;
   long long rebases_ = 0;  // FP32-bulk inner solves ended at the rejection limit and re-based
+  BatchHook *batch_ = nullptr;  // batched form: the scheduler that runs this solver's inner solves
+  int batch_idx_ = -1;
   bool ready_ = false, solved_once_ = false, has_x0_ = false, has_l0_ = false, own_stream_ = false;
   bool tuned_ = false;
   std::vector<double> h_x0_, h_l0_;
