@@ -24,7 +24,7 @@ _lib = None
 
 SNAP_SCALARS = 8
 CHK_COLS = 14
-OTR_COLS = 24
+OTR_COLS = 25
 STATUS = {0: "SOLVED", 1: "PRIMAL_INFEASIBLE", 2: "DUAL_INFEASIBLE", 3: "ITER_LIMIT", 4: "TIME_LIMIT",
           5: "NUMERICAL_ERROR"}
 
@@ -351,7 +351,7 @@ def solve_traced(inst: dict, max_rows: int = 10000, x0=None, lam0=None, **params
     info["status_name"] = STATUS.get(info["status"], "?")
     names = ["k", "primal_ok", "r_inf", "dx_inf", "sc_rp", "sc_rd", "sc_sp", "sc_sd", "un_rp", "un_rd", "un_sp",
              "un_sd", "gamma", "ratio", "rho", "dta", "dtr", "dta_after", "dtr_after", "eak", "erk", "eak_after",
-             "erk_after", "moved"]
+             "erk_after", "moved", "sd_in"]
     tr = []
     for row, v in zip(rows[:nr.value], vecs[:nr.value]):
         d = dict(zip(names, row))

@@ -669,6 +669,7 @@ typedef struct {
 
 typedef struct {
   long long trials, accepted, restarts;
+  double sd_in; /* s_d^in (Eq. inner-scales) of the candidate an inner solve returned */
 } ctr_t;
 
 static double now_seconds(void);
@@ -785,8 +786,8 @@ static int inner_solve(const sqp_t *S, const or_params *prm, const double *z, co
       int okc = Rc.rp <= dta + dtr * Rc.sp && Rc.rd <= dta + dtr * Rc.sd;
       int oka = Ra.rp <= dta + dtr * Ra.sp && Ra.rd <= dta + dtr * Ra.sd;
       if (!(D && D->ignore_convergence)) {
-        if (okc) { status = IN_CONVERGED; ret_w = w; ret_y = yy; goto done; }
-        if (oka) { status = IN_CONVERGED; ret_w = wb; ret_y = yb; goto done; }
+        if (okc) { status = IN_CONVERGED; ret_w = w; ret_y = yy; C->sd_in = Rc.sd; goto done; }
+        if (oka) { status = IN_CONVERGED; ret_w = wb; ret_y = yb; C->sd_in = Ra.sd; goto done; }
       }
       if (!D && ttot == kin) break;
       /* Restart test (reading of Sec. 3.3.7) and primal weight (Eq. primal-weight-update). */
@@ -1107,11 +1108,11 @@ static void state_free(state_t *T) {
  *   [8..11] the same on the original data, [12] gamma, [13] the ratio of Eq.
  *   inner-tolerance-factor, [14] rho_in, [15..16] delta_a, delta_r before,
  *   [17..18] after, [19..20] eps_a,k, eps_r,k before, [21..22] after,
- *   [23] center moved
+ *   [23] center moved, [24] s_d^in of the candidate the inner solve returned
  * and the vectors [x^{k+1} | z^k | z after the center update | lambda^{k+1} |
  * sigma before | sigma after | r | r of the previous iteration] (n, n, n, m,
  * m, m, m, m entries) in the scaled internal coordinates (rows E then I). */
-#define OTR_COLS 24
+#define OTR_COLS 25
 typedef struct {
   int max_rows, n_rows;
   double *rows, *vecs;
@@ -1224,7 +1225,7 @@ static int solve_impl(const or_problem *P, const or_params *prm, double *x_out, 
     dta = dmax(dta * rho, prm->tol_floor * prm->eps_abs);
     dtr = dmax(dtr * rho, prm->tol_floor * prm->eps_rel);
     if (trow) {
-      trow[3] = dx; trow[13] = ratio; trow[14] = rho; trow[17] = dta; trow[18] = dtr;
+      trow[3] = dx; trow[13] = ratio; trow[14] = rho; trow[17] = dta; trow[18] = dtr; trow[24] = C.sd_in;
       memcpy(tvec + 3 * (size_t)n + 2 * (size_t)m, T.sig, sizeof(double) * m);
     }
     if (prm->verbose) {

@@ -39,18 +39,33 @@ def make_instance(seed: int, n: int, shift: float = None) -> dict:
     return I.mid_qp(seed, n=n, m=n // 2, replica_n=min(3000, n), shift=shift)
 
 
-def generate_batched(count, rng, n_min, n_max, *, eps, explore, time_limit, threads, chunk=64):
-    """Training trajectories solved concurrently (pdnqp_solve_batch), `chunk`
+def _make_args(a):
+    return make_instance(*a)
+
+
+def make_instances(specs, procs=0):
+    """Instances for (seed, n, shift) specs, in a pool of `procs` processes
+    (spawned: no copy of a CUDA context) when procs > 1."""
+    if procs <= 1 or len(specs) < 2:
+        return [make_instance(*sp) for sp in specs]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_make_args, specs, chunksize=1)
+
+
+def generate_batched(count, rng, n_min, n_max, *, eps, explore, time_limit, threads, chunk=64, procs=0):
+    """Training trajectories solved together (pdnqp_solve_batch), `chunk`
     problems at a time; the instances share the diagonal shift of the first
-    (same density), which saves the replica eigen-decomposition per instance."""
-    shift = None
+    (same density), which saves the replica eigen-decomposition per instance,
+    and are built in `procs` processes."""
+    ns = [int(rng.integers(n_min, n_max + 1)) for _ in range(count)]
+    shift = make_instance(10_000, ns[0])["shift"] if count else None
     data = []
     for c0 in range(0, count, chunk):
+        idx = list(range(c0, min(count, c0 + chunk)))
+        insts = make_instances([(10_000 + i, ns[i], shift) for i in idx], procs)
         hs = []
-        for i in range(c0, min(count, c0 + chunk)):
-            n = int(rng.integers(n_min, n_max + 1))
-            inst = make_instance(10_000 + i, n, shift=shift)
-            shift = inst["shift"]
+        for i, inst in zip(idx, insts):
             h = P.create_from_instance(inst, precision=32)
             P.pdnqp_set_param(h, "time_limit", time_limit)
             P.pdnqp_set_param(h, "ctrl_explore", explore)
@@ -61,6 +76,50 @@ def generate_batched(count, rng, n_min, n_max, *, eps, explore, time_limit, thre
             data += transitions(P.pdnqp_get_trace(h))
             h.close()
     return data
+
+
+def evaluate_batched(insts, theta, *, eps, time_limit, chunk=64):
+    """The rules and the network on the same instances (paired), each side
+    solved as fused batches; per instance the status, outer and inner
+    iterations and the relative KKT residual of both sides."""
+    out = []
+    for c0 in range(0, len(insts), chunk):
+        sub = insts[c0:c0 + chunk]
+        res = {}
+        for side in ("rule", "mlp"):
+            hs = []
+            for inst in sub:
+                h = P.create_from_instance(inst, precision=32)
+                P.pdnqp_set_param(h, "time_limit", time_limit)
+                if side == "mlp":
+                    P.pdnqp_set_controller(h, theta)
+                    P.pdnqp_set_param(h, "controller", 1)
+                hs.append(h)
+            sts = P.pdnqp_solve_batch(hs, eps, eps)
+            rows = []
+            for h, st in zip(hs, sts):
+                x, y, r = P.pdnqp_get(h)
+                rows.append({"status": P.STATUS_NAMES[st], "outer": r["outer_iters"], "inner": r["inner_iters"],
+                             "rel_kkt": r["rel_kkt"], "ctrl_used": r["ctrl_used"], "x": x, "y": y})
+                h.close()
+            res[side] = rows
+        for inst, a, b in zip(sub, res["rule"], res["mlp"]):
+            out.append({"n": inst["Q"].shape[0], "rule": a, "mlp": b})
+    return out
+
+
+def sign_test(d):
+    """Two-sided exact sign test of the paired differences d (zeros dropped):
+    (count of negatives, count of nonzero, p-value)."""
+    from math import comb
+    d = np.asarray(d)
+    d = d[d != 0]
+    k, nn = int((d < 0).sum()), int(d.size)
+    if nn == 0:
+        return 0, 0, 1.0
+    lo = min(k, nn - k)
+    p = min(1.0, 2.0 * sum(comb(nn, i) for i in range(lo + 1)) / 2.0 ** nn)
+    return k, nn, p
 
 
 def run(inst: dict, *, precision=32, eps=1e-4, controller=None, explore=0.0, seed=0, time_limit=60.0, stream=None):
@@ -150,18 +209,24 @@ def main():
     ap.add_argument("--eval-n-min", type=int, default=None)
     ap.add_argument("--eval-n-max", type=int, default=None)
     ap.add_argument("--compare", default=None, help="weights (.npy) evaluated on the same instances too")
+    ap.add_argument("--procs", type=int, default=0, help="processes that build the instances")
+    ap.add_argument("--eval-batched", action="store_true",
+                    help="paired evaluation with fused batches (iteration counts; no per-problem wall time)")
+    ap.add_argument("--weights", default=None, help="evaluate these weights (.npy) instead of training")
     a = ap.parse_args()
     P.load()
     rng = np.random.default_rng(np.random.SeedSequence([2024, 7]))
     t0 = time.perf_counter()
-    if a.data and os.path.exists(a.data):
+    if a.weights:
+        feats = acts = scores = []
+    elif a.data and os.path.exists(a.data):
         z = np.load(a.data)
         feats, acts, scores = z["feats"], z["acts"], z["scores"]
         for _ in range(a.train):  # keep the evaluation sizes of a fresh run
             rng.integers(a.n_min, a.n_max + 1)
     elif a.threads > 0:
         data = generate_batched(a.train, rng, a.n_min, a.n_max, eps=a.eps, explore=a.explore,
-                                time_limit=a.time_limit, threads=a.threads)
+                                time_limit=a.time_limit, threads=a.threads, procs=a.procs)
         feats, acts, scores = (np.array(v) for v in zip(*data))
         if a.data:
             np.savez(a.data, feats=feats, acts=acts, scores=scores)
@@ -175,12 +240,38 @@ def main():
         if a.data:
             np.savez(a.data, feats=feats, acts=acts, scores=scores)
     gen_s = time.perf_counter() - t0
-    theta, hist = train(feats, acts, scores)
+    if a.weights:
+        theta, hist = np.load(a.weights).astype(np.float32), []
+    else:
+        theta, hist = train(feats, acts, scores)
     if a.out:
         np.save(a.out, theta)
     rows = []
     e_lo = a.eval_n_min if a.eval_n_min else a.n_min
     e_hi = a.eval_n_max if a.eval_n_max else a.n_max
+    if a.eval_batched:
+        ns = [int(rng.integers(e_lo, e_hi + 1)) for _ in range(a.eval)]
+        shift = make_instance(90_000, ns[0])["shift"] if a.eval else None
+        insts = make_instances([(90_000 + j, ns[j], shift) for j in range(a.eval)], a.procs)
+        ev = evaluate_batched(insts, theta, eps=a.eps, time_limit=a.time_limit)
+        both = [e for e in ev if e["rule"]["status"] == e["mlp"]["status"] == "SOLVED"]
+        summary = {}
+        for key in ("outer", "inner"):
+            d = [e["mlp"][key] - e["rule"][key] for e in both]
+            k, nn, p = sign_test(d)
+            summary[key] = {"rule_total": int(sum(e["rule"][key] for e in both)),
+                            "mlp_total": int(sum(e["mlp"][key] for e in both)),
+                            "mlp_fewer": k, "nonzero": nn, "sign_test_p": p,
+                            "median_ratio": float(np.median([e["mlp"][key] / max(1, e["rule"][key]) for e in both]))
+                            if both else None}
+        print(json.dumps({"trajectories": a.train, "transitions": len(scores), "generation_s": gen_s, "loss": hist,
+                          "eval_instances": a.eval, "both_solved": len(both),
+                          "statuses": [[e["rule"]["status"], e["mlp"]["status"]] for e in ev],
+                          "paired": summary,
+                          "rows": [{"n": e["n"], **{f"{s}_{k}": e[s][k] for s in ("rule", "mlp")
+                                                    for k in ("outer", "inner", "rel_kkt", "ctrl_used")}}
+                                   for e in ev]}, default=float))
+        return
     for j in range(a.eval):
         n = int(rng.integers(e_lo, e_hi + 1))
         inst = make_instance(90_000 + j, n)

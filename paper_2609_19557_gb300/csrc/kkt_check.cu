@@ -73,7 +73,9 @@ double *g_noalloc_ptr[kMaxDevices] = {};
 
 // Device address of the static scratch on the current device.  In host code
 // the array's name is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
+// once per device (with that device current) and cached for the life of the
+// process (a cudaDeviceReset, which unloads the module, invalidates it; the
+// header tells callers not to use this entry point on a reset device).
 int noalloc_scratch(double **out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);

@@ -1,8 +1,10 @@
 """Parity at the benchmark's full size (n = 1e6, m = 5e5) in the launch
 configuration bench.py times (persistent trial loop, 3 blocks/SM in FP32):
-the first inner iterations against the oracle's own run of the same
-iterations (FP64 within 1e-10, FP32-bulk within 1e-4 relative), and the
-solver's reported residuals against the oracle's external KKT test."""
+the inner iterations against the oracle's own run of the same iterations
+(FP64 within 1e-10 through 130 accepted iterations, past the periodic checks
+at 64 and 128 with their restart decisions and primal-weight updates;
+FP32-bulk within 1e-4 relative over the first iterations), and the solver's
+reported residuals against the oracle's external KKT test."""
 import numpy as np
 import pytest
 
@@ -10,7 +12,8 @@ from paper_2609_19557_gb300 import instances as I
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
-CK = [1, 2, 3, 5]
+CK = [1, 2, 3, 5, 63, 64, 65, 127, 128, 129, 130]
+CK32 = [1, 2, 3, 5]
 
 
 @pytest.fixture(scope="module")
@@ -39,16 +42,26 @@ def rel_err(a, b):
 
 
 @pytest.mark.parametrize("precision,tol", [(64, 1e-10), (32, 1e-4)])
-def test_full_size_first_iterations(P, large, ref, precision, tol):
+def test_full_size_iterations(P, large, ref, precision, tol):
     snaps, info = ref
+    ck = CK if precision == 64 else CK32
     h = P.create_from_instance(large, precision=precision)
-    gpu = P.pdnqp_debug_inner(h, CK)
+    gpu = P.pdnqp_debug_inner(h, ck)
     assert abs(P.pdnqp_get_param(h, "gamma") - info["gamma"]) <= 1e-10 * info["gamma"]
     h.close()
-    for s, r, c in zip(gpu, snaps, CK):
+    assert len(gpu) == len(ck)
+    for s, r, c in zip(gpu, snaps, ck):
         assert s["t_total"] == r["t_total"] == c
         e = max(rel_err(s[k], r[k]) for k in ("w", "y", "wbar", "ybar"))
         assert e <= tol, (precision, c, e)
+        if precision == 64:
+            # decisions of Eq. adaptive-condition, of the restart test and of
+            # Eq. primal-weight-update at the checks of iterations 64 and 128
+            assert s["trials"] == r["trials"] and s["restarts"] == r["restarts"], (c, s["trials"], r["trials"])
+            assert s["t"] == r["t"] and s["kappa"] == r["kappa"], c
+            assert abs(s["omega"] - r["omega"]) <= tol * abs(r["omega"]), (c, s["omega"], r["omega"])
+    if precision == 64:
+        assert snaps[-1]["restarts"] >= 1  # the window covers a restart
 
 
 def test_full_size_residuals_match_external_test(P, oracle, large):

@@ -148,6 +148,7 @@ def test_inner_tolerance_factor(outer):
         ratio = min(1.0, (dx / t["gamma"]) / t["sc_rd"]) if t["sc_rd"] > 0 else 1.0
         rho = RHO_MAX - (RHO_MAX - RHO_MIN) * ratio
         assert _rel(t["rho"], rho) < 1e-12
+        assert t["sd_in"] >= 1.0  # Eq. inner-scales include 1
         assert _rel(t["dta_after"], max(t["dta"] * rho, TOL_FLOOR * eps)) < 1e-12
         assert _rel(t["dtr_after"], max(t["dtr"] * rho, TOL_FLOOR * eps)) < 1e-12
         floor_hit += t["dta"] * rho < TOL_FLOOR * eps
