@@ -50,7 +50,8 @@ def parse():
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--precision", type=int, default=32, choices=[32, 64])
     p.add_argument("--budget", type=int, default=2000, help="accepted inner iterations per step")
-    p.add_argument("--ttk", type=float, default=0.0, help="also time a solve to rel-KKT 1e-4 (cap in seconds)")
+    p.add_argument("--ttk", type=float, default=90.0,
+                   help="also time solves to rel-KKT 1e-4, each capped at this many seconds (0: skip)")
     p.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU (oracle) baseline leg")
     p.add_argument("--loop", default="persistent", choices=["persistent", "cond", "unrolled"],
@@ -62,6 +63,8 @@ def parse():
     p.add_argument("--batch-time-limit", type=float, default=5.0, help="seconds per problem")
     p.add_argument("--batch-median", type=float, default=1e4, help="median n of the batch's log-normal sizes")
     p.add_argument("--batch-sigma", type=float, default=1.0, help="log-std of the batch's sizes")
+    p.add_argument("--batch-procs", type=int, default=min(16, os.cpu_count() or 1),
+                   help="processes that build the batch's problems")
     p.add_argument("--solve-times", action="store_true",
                    help="instead: end-to-end solve times of the GPU forms and the oracle on the n=200 and "
                         "n=50,000 workloads")
@@ -75,6 +78,22 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def captured_traffic(precision, trials_per_launch):
+    """DRAM bytes (read + write) per launch of the trial loop from the committed
+    ncu capture (profiles/traffic_trials_fp{32,64}.json) scaled to the launch's
+    trials, or None when the kernel sources changed since the capture."""
+    tr_path = os.path.join(ROOT, "profiles", f"traffic_trials_fp{precision}.json")
+    if not os.path.exists(tr_path):
+        return None
+    tj = json.load(open(tr_path))
+    hsh = hashlib.sha256()
+    for f in tj.get("source_files", []):
+        hsh.update(open(os.path.join(ROOT, f), "rb").read())
+    if tj.get("source_sha256") != hsh.hexdigest() or not tj.get("dram_bytes_per_trial"):
+        return None
+    return tj["dram_bytes_per_trial"] * trials_per_launch
 
 
 def trial_bytes(inst, v):
@@ -247,17 +266,7 @@ def run_native(args):
         bpt = trial_bytes(inst, 4 if args.precision == 32 else 8)
         achieved = bpt * loop_trials / loop_s / 1e9
         per_launch = loop_trials / max(1, loop_launches)
-        traffic = None
-        tr_path = os.path.join(ROOT, "profiles", f"traffic_trials_fp{args.precision}.json")
-        if os.path.exists(tr_path):
-            # Counters of one ncu capture, valid only while the kernel sources
-            # are the ones they were taken on.
-            tj = json.load(open(tr_path))
-            hsh = hashlib.sha256()
-            for f in tj.get("source_files", []):
-                hsh.update(open(os.path.join(ROOT, f), "rb").read())
-            if tj.get("source_sha256") == hsh.hexdigest() and tj.get("dram_bytes_per_trial"):
-                traffic = tj["dram_bytes_per_trial"] * per_launch
+        traffic = captured_traffic(args.precision, per_launch)
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "k_trials (persistent trial loop: primal, row and column passes, "
                 "acceptance decision)", "peak_source": peak_src,
@@ -297,13 +306,14 @@ def run_native(args):
         torch.cuda.synchronize()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
-        it64, ls64, lt64 = 0, 0.0, 0
+        it64, ls64, lt64, ll64 = 0, 0.0, 0, 0
         for _ in range(max(1, args.steps // 2)):
             P.pdnqp_solve(h64, 1e-4, 1e-4)
             r64 = P.pdnqp_get(h64)[2]
             it64 += r64["inner_iters"]
             ls64 += r64["loop_seconds"]
             lt64 += r64["loop_trials"]
+            ll64 += r64["loop_launches"]
         a1.record(stream)
         torch.cuda.synchronize()
         compare = {"fp64_iters_per_s": it64 / (a0.elapsed_time(a1) / 1e3)}
@@ -314,7 +324,11 @@ def run_native(args):
             ach64 = b64 * lt64 / ls64 / 1e9
             compare["roofline"] = {"bound": "hbm", "achieved": ach64, "peak": peak, "unit": "GB/s",
                                    "frac": ach64 / peak, "kernel": "k_trials<double>",
-                                   "algorithmic_bytes_per_trial": b64, "us_per_trial": 1e6 * ls64 / lt64}
+                                   "traffic": captured_traffic(64, lt64 / max(1, ll64)),
+                                   "algorithmic_bytes_per_trial": b64, "us_per_trial": 1e6 * ls64 / lt64,
+                                   "trials_per_launch": lt64 / max(1, ll64),
+                                   "fp64_pipe": "the FP64 pipe is 67 % busy in this kernel (ncu, "
+                                                "profiles/k_trials_n1e6_fp64.md): it binds before HBM"}
         h64.close()
 
     ttk = None
@@ -335,7 +349,8 @@ def run_native(args):
             st = P.pdnqp_solve(h3, 1e-4, 1e-4)
             _, _, r3 = P.pdnqp_get(h3)
             ttk[name] = {"status": P.STATUS_NAMES[st], "seconds": r3["solve_seconds"], "rel_kkt": r3["rel_kkt"],
-                         "outer_iters": r3["outer_iters"], "inner_iters": r3["inner_iters"]}
+                         "outer_iters": r3["outer_iters"], "inner_iters": r3["inner_iters"], "cap_s": args.ttk,
+                         "time_to_1e-4_s": r3["solve_seconds"] if P.STATUS_NAMES[st] == "SOLVED" else None}
             h3.close()
 
     cpu = None
@@ -448,6 +463,23 @@ def batch_totals(ws, wall, solved, inner, device):
     return float(t.item()), int(round(c[0].item())), int(round(c[1].item()))
 
 
+def _batch_one(a):
+    from paper_2609_19557_gb300 import instances as I
+    count, k, med, sig = a
+    return I.batched_set(0, count=count, only=[k], n_median=med, sigma=sig)[0]
+
+
+def batch_instances(count, positions, median, sigma, procs):
+    """The batch's problems at `positions`, built in `procs` spawned processes
+    (each problem has its own seed, so the result does not depend on procs)."""
+    from paper_2609_19557_gb300 import instances as I
+    if procs <= 1:
+        return I.batched_set(0, count=count, only=positions, n_median=median, sigma=sigma)
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_batch_one, [(count, k, median, sigma) for k in positions], chunksize=1)
+
+
 def run_batch(args):
     """Batched form: `args.batch` independent problems (sizes lognormal in
     [1e3, 1e5] with median --batch-median and log-std --batch-sigma; half from
@@ -466,8 +498,8 @@ def run_batch(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     P.load()
     t = time.perf_counter()
-    insts = I.batched_set(0, count=args.batch, only=batch_shard(args.batch, ws, rank),
-                          n_median=args.batch_median, sigma=args.batch_sigma)
+    insts = batch_instances(args.batch, batch_shard(args.batch, ws, rank), args.batch_median, args.batch_sigma,
+                            args.batch_procs)
     gen_s = time.perf_counter() - t
     t = time.perf_counter()
     hs = []

@@ -43,14 +43,16 @@ def _make_args(a):
     return make_instance(*a)
 
 
-def make_instances(specs, procs=0):
-    """Instances for (seed, n, shift) specs, in a pool of `procs` processes
-    (spawned: no copy of a CUDA context) when procs > 1."""
+def make_instances(specs, procs=0, pool=None):
+    """Instances for (seed, n, shift) specs, in `pool` or in a pool of `procs`
+    processes (spawned: no copy of a CUDA context) when procs > 1."""
+    if pool is not None:
+        return pool.map(_make_args, specs, chunksize=1)
     if procs <= 1 or len(specs) < 2:
         return [make_instance(*sp) for sp in specs]
     import multiprocessing as mp
-    with mp.get_context("spawn").Pool(procs) as pool:
-        return pool.map(_make_args, specs, chunksize=1)
+    with mp.get_context("spawn").Pool(procs) as pl:
+        return pl.map(_make_args, specs, chunksize=1)
 
 
 def generate_batched(count, rng, n_min, n_max, *, eps, explore, time_limit, threads, chunk=64, procs=0):
@@ -61,9 +63,13 @@ def generate_batched(count, rng, n_min, n_max, *, eps, explore, time_limit, thre
     ns = [int(rng.integers(n_min, n_max + 1)) for _ in range(count)]
     shift = make_instance(10_000, ns[0])["shift"] if count else None
     data = []
+    pool = None
+    if procs > 1:
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(procs)
     for c0 in range(0, count, chunk):
         idx = list(range(c0, min(count, c0 + chunk)))
-        insts = make_instances([(10_000 + i, ns[i], shift) for i in idx], procs)
+        insts = make_instances([(10_000 + i, ns[i], shift) for i in idx], procs, pool)
         hs = []
         for i, inst in zip(idx, insts):
             h = P.create_from_instance(inst, precision=32)
@@ -75,6 +81,9 @@ def generate_batched(count, rng, n_min, n_max, *, eps, explore, time_limit, thre
         for h in hs:
             data += transitions(P.pdnqp_get_trace(h))
             h.close()
+    if pool is not None:
+        pool.close()
+        pool.join()
     return data
 
 
@@ -219,6 +228,8 @@ def main():
     t0 = time.perf_counter()
     if a.weights:
         feats = acts = scores = []
+        for _ in range(a.train):  # the evaluation sizes of a run that trained on a.train trajectories
+            rng.integers(a.n_min, a.n_max + 1)
     elif a.data and os.path.exists(a.data):
         z = np.load(a.data)
         feats, acts, scores = z["feats"], z["acts"], z["scores"]
