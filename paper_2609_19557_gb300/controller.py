@@ -22,6 +22,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import sys
 import time
 
 import numpy as np
@@ -55,7 +56,23 @@ def make_instances(specs, procs=0, pool=None):
         return pl.map(_make_args, specs, chunksize=1)
 
 
-def generate_batched(count, rng, n_min, n_max, *, eps, explore, time_limit, threads, chunk=64, procs=0):
+def create_all(insts, setup, threads=16):
+    """Handles for `insts` (FP32-bulk), created by `threads` host threads at
+    once (each creation runs on its own stream; the C calls release the GIL),
+    then set up by setup(k, handle)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(k):
+        h = P.create_from_instance(insts[k], precision=32)
+        setup(k, h)
+        return h
+
+    with ThreadPoolExecutor(max(1, threads)) as ex:
+        return list(ex.map(one, range(len(insts))))
+
+
+def generate_batched(count, rng, n_min, n_max, *, eps, explore, time_limit, threads, chunk=64, procs=0,
+                     progress=None, budget_s=float("inf")):
     """Training trajectories solved together (pdnqp_solve_batch), `chunk`
     problems at a time; the instances share the diagonal shift of the first
     (same density), which saves the replica eigen-decomposition per instance,
@@ -67,20 +84,25 @@ def generate_batched(count, rng, n_min, n_max, *, eps, explore, time_limit, thre
     if procs > 1:
         import multiprocessing as mp
         pool = mp.get_context("spawn").Pool(procs)
+    t_start = time.perf_counter()
     for c0 in range(0, count, chunk):
+        if time.perf_counter() - t_start > budget_s:
+            break  # the generation budget is spent: train on the trajectories so far
         idx = list(range(c0, min(count, c0 + chunk)))
         insts = make_instances([(10_000 + i, ns[i], shift) for i in idx], procs, pool)
-        hs = []
-        for i, inst in zip(idx, insts):
-            h = P.create_from_instance(inst, precision=32)
+
+        def setup(k, h):
             P.pdnqp_set_param(h, "time_limit", time_limit)
             P.pdnqp_set_param(h, "ctrl_explore", explore)
-            P.pdnqp_set_param(h, "ctrl_seed", i)
-            hs.append(h)
+            P.pdnqp_set_param(h, "ctrl_seed", idx[k])
+
+        hs = create_all(insts, setup, max(1, threads))
         P.pdnqp_solve_batch(hs, eps, eps, threads=threads)
         for h in hs:
             data += transitions(P.pdnqp_get_trace(h))
             h.close()
+        if progress:
+            progress(idx[-1] + 1, data)
     if pool is not None:
         pool.close()
         pool.join()
@@ -96,14 +118,13 @@ def evaluate_batched(insts, theta, *, eps, time_limit, chunk=64):
         sub = insts[c0:c0 + chunk]
         res = {}
         for side in ("rule", "mlp"):
-            hs = []
-            for inst in sub:
-                h = P.create_from_instance(inst, precision=32)
+            def setup(k, h, side=side):
                 P.pdnqp_set_param(h, "time_limit", time_limit)
                 if side == "mlp":
                     P.pdnqp_set_controller(h, theta)
                     P.pdnqp_set_param(h, "controller", 1)
-                hs.append(h)
+
+            hs = create_all(sub, setup)
             sts = P.pdnqp_solve_batch(hs, eps, eps)
             rows = []
             for h, st in zip(hs, sts):
@@ -222,9 +243,12 @@ def main():
     ap.add_argument("--eval-batched", action="store_true",
                     help="paired evaluation with fused batches (iteration counts; no per-problem wall time)")
     ap.add_argument("--weights", default=None, help="evaluate these weights (.npy) instead of training")
+    ap.add_argument("--gen-budget", type=float, default=float("inf"),
+                    help="seconds after which no new chunk of training trajectories starts")
     a = ap.parse_args()
     P.load()
     rng = np.random.default_rng(np.random.SeedSequence([2024, 7]))
+    gen_done = [a.train]  # training trajectories actually generated (a generation budget may cut them)
     t0 = time.perf_counter()
     if a.weights:
         feats = acts = scores = []
@@ -236,8 +260,17 @@ def main():
         for _ in range(a.train):  # keep the evaluation sizes of a fresh run
             rng.integers(a.n_min, a.n_max + 1)
     elif a.threads > 0:
+        def progress(done, data):
+            gen_done[0] = done
+            print(json.dumps({"trajectories_done": done, "transitions": len(data),
+                              "seconds": time.perf_counter() - t0}), file=sys.stderr, flush=True)
+            if a.data:
+                f, ac, sc = (np.array(v) for v in zip(*data))
+                np.savez(a.data, feats=f, acts=ac, scores=sc)
+
         data = generate_batched(a.train, rng, a.n_min, a.n_max, eps=a.eps, explore=a.explore,
-                                time_limit=a.time_limit, threads=a.threads, procs=a.procs)
+                                time_limit=a.time_limit, threads=a.threads, procs=a.procs, progress=progress,
+                                budget_s=a.gen_budget)
         feats, acts, scores = (np.array(v) for v in zip(*data))
         if a.data:
             np.savez(a.data, feats=feats, acts=acts, scores=scores)
@@ -275,7 +308,7 @@ def main():
                             "mlp_fewer": k, "nonzero": nn, "sign_test_p": p,
                             "median_ratio": float(np.median([e["mlp"][key] / max(1, e["rule"][key]) for e in both]))
                             if both else None}
-        print(json.dumps({"trajectories": a.train, "transitions": len(scores), "generation_s": gen_s, "loss": hist,
+        print(json.dumps({"trajectories": gen_done[0], "transitions": len(scores), "generation_s": gen_s, "loss": hist,
                           "eval_instances": a.eval, "both_solved": len(both),
                           "statuses": [[e["rule"]["status"], e["mlp"]["status"]] for e in ev],
                           "paired": summary,
