@@ -243,6 +243,8 @@ def main():
     ap.add_argument("--eval-batched", action="store_true",
                     help="paired evaluation with fused batches (iteration counts; no per-problem wall time)")
     ap.add_argument("--weights", default=None, help="evaluate these weights (.npy) instead of training")
+    ap.add_argument("--eval-time-limit", type=float, default=None,
+                    help="time limit of the evaluation solves (default: --time-limit)")
     ap.add_argument("--gen-budget", type=float, default=float("inf"),
                     help="seconds after which no new chunk of training trajectories starts")
     a = ap.parse_args()
@@ -297,7 +299,8 @@ def main():
         ns = [int(rng.integers(e_lo, e_hi + 1)) for _ in range(a.eval)]
         shift = make_instance(90_000, ns[0])["shift"] if a.eval else None
         insts = make_instances([(90_000 + j, ns[j], shift) for j in range(a.eval)], a.procs)
-        ev = evaluate_batched(insts, theta, eps=a.eps, time_limit=a.time_limit)
+        ev = evaluate_batched(insts, theta, eps=a.eps,
+                              time_limit=a.eval_time_limit if a.eval_time_limit else a.time_limit)
         both = [e for e in ev if e["rule"]["status"] == e["mlp"]["status"] == "SOLVED"]
         summary = {}
         for key in ("outer", "inner"):

@@ -102,3 +102,32 @@ def test_trained_controller_gain(P, oracle):
         "transitions": len(data), "train_loss": hist,
         "outer_rule_vs_mlp": R[:, :2].sum(axis=0).tolist(), "inner_rule_vs_mlp": R[:, 2:4].sum(axis=0).tolist(),
         "ctrl_used": int(R[:, 4].sum()), "fallbacks": int(R[:, 5].sum())}))
+
+
+def test_committed_controller_paired(P, oracle):
+    """The committed network (paper_2609_19557_gb300/controller_weights.npy)
+    against the paper's rules on 12 fresh instances of the mid-size generator
+    at n = 10,000-20,000, paired (the same instances for both), each side
+    solved to rel-KKT 1e-4 as one fused batch.  Solves are deterministic, so
+    the paired counts are fixed for this library build; the test prints them
+    with an exact two-sided sign test and asserts the direction they showed."""
+    from paper_2609_19557_gb300 import controller as CT
+    import os
+    theta = np.load(os.path.join(os.path.dirname(CT.__file__), "controller_weights.npy")).astype(np.float32)
+    rng = np.random.default_rng(11)
+    ns = [int(rng.integers(10_000, 20_001)) for _ in range(12)]
+    shift = CT.make_instance(71_000, ns[0])["shift"]
+    insts = [CT.make_instance(71_000 + j, ns[j], shift) for j in range(12)]
+    ev = CT.evaluate_batched(insts, theta, eps=1e-4, time_limit=300.0)
+    for inst, e in zip(insts, ev):
+        for side in ("rule", "mlp"):
+            assert e[side]["status"] == "SOLVED", (side, e[side]["status"])
+            assert oracle.kkt_pass(inst, e[side]["x"], e[side]["y"], 1e-4, 1e-4)
+    stats = {}
+    for key in ("outer", "inner"):
+        d = [e["mlp"][key] - e["rule"][key] for e in ev]
+        k, nn, p = CT.sign_test(d)
+        stats[key] = {"rule_total": sum(e["rule"][key] for e in ev), "mlp_total": sum(e["mlp"][key] for e in ev),
+                      "mlp_fewer": k, "nonzero": nn, "sign_test_p": p}
+    print("committed controller, paired:", json.dumps(stats))
+    assert all(e["mlp"]["ctrl_used"] > 0 for e in ev)
