@@ -109,8 +109,13 @@ def test_committed_controller_paired(P, oracle):
     against the paper's rules on 12 fresh instances of the mid-size generator
     at n = 10,000-20,000, paired (the same instances for both), each side
     solved to rel-KKT 1e-4 as one fused batch.  Solves are deterministic, so
-    the paired counts are fixed for this library build; the test prints them
-    with an exact two-sided sign test and asserts the direction they showed."""
+    the paired counts are fixed for this library build.  Measured on the
+    GB300: the network's totals are lower (outer 9,026 vs 9,595, inner
+    1,089,728 vs 1,175,744), but it needs fewer outer iterations on only 6 of
+    the 12 instances (exact two-sided sign test p = 1.0; inner 7 of 12,
+    p = 0.77), as on the 32-instance evaluation (p = 0.60): the direction of
+    the totals holds, with no confidence that it generalises instance by
+    instance.  The test asserts the totals' direction and prints the test."""
     from paper_2609_19557_gb300 import controller as CT
     import os
     theta = np.load(os.path.join(os.path.dirname(CT.__file__), "controller_weights.npy")).astype(np.float32)
@@ -131,3 +136,5 @@ def test_committed_controller_paired(P, oracle):
                       "mlp_fewer": k, "nonzero": nn, "sign_test_p": p}
     print("committed controller, paired:", json.dumps(stats))
     assert all(e["mlp"]["ctrl_used"] > 0 for e in ev)
+    assert stats["outer"]["mlp_total"] < stats["outer"]["rule_total"]
+    assert stats["inner"]["mlp_total"] < stats["inner"]["rule_total"]
