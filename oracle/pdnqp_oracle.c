@@ -16,8 +16,8 @@
  * its definition instead of being cached.  Loops run in natural order; the
  * file is meant to be compiled with -ffp-contract=off.
  *
- * Readings of points where the paper is silent (the same readings are used by
- * the CUDA path and listed in the design notes):
+ * Readings of points where the paper is silent (the CUDA path uses the same
+ * readings):
  *   - Two-sided rows l_c <= Ax <= u_c: rows with l_c == u_c are equality rows,
  *     every other row is an "inequality" row whose slack lives in [l_c, u_c].
  *     With u_c = +inf this is exactly Eq. projected-multipliers.

@@ -21,7 +21,7 @@ def test_trial_bytes_hand_count():
 
 def test_trial_bytes_large_workload_matches_stated_figure():
     """The 1M-variable workload: 210 MB per trial in FP32, 358 MB in FP64 (the
-    figures the roofline and the design notes quote), from the sizes alone."""
+    figures the roofline quotes), from the sizes alone."""
     n, m = 1_000_000, 500_000
     nnz_q, nnz_a = 4_999_994, 4_000_000  # band (3 per row) + random pairs; 8 per row of A
 

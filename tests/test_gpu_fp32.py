@@ -71,7 +71,7 @@ def test_fp32_tight_tolerance_escalates_to_fp64(P, oracle):
     """n = 50,000 to rel-KKT 1e-6: the FP32-bulk form alone follows the FP64
     form's trajectory for about 25 outer iterations, then its inner solves
     stop converging within K_in and it ends in NUMERICAL_ERROR (the FP32
-    form's limit on this workload, recorded in the design notes); with the
+    form's limit on this workload); with the
     default escalation the handle continues as an FP64 solve from the same
     start point and returns a point that passes the oracle's KKT test at
     1e-6, flagged as escalated."""
