@@ -65,6 +65,10 @@ def parse():
     p.add_argument("--batch-sigma", type=float, default=1.0, help="log-std of the batch's sizes")
     p.add_argument("--batch-procs", type=int, default=min(16, os.cpu_count() or 1),
                    help="processes that build the batch's problems")
+    p.add_argument("--batch-mix", default="alternate", choices=["alternate", "small"],
+                   help="alternate: half small generator, half Motzkin-Straus; small: small generator only")
+    p.add_argument("--batch-compare", action="store_true",
+                   help="also solve the whole batch in the thread-pool form (fresh handles) and report both walls")
     p.add_argument("--solve-times", action="store_true",
                    help="instead: end-to-end solve times of the GPU forms and the oracle on the n=200 and "
                         "n=50,000 workloads")
@@ -465,19 +469,38 @@ def batch_totals(ws, wall, solved, inner, device):
 
 def _batch_one(a):
     from paper_2609_19557_gb300 import instances as I
-    count, k, med, sig = a
-    return I.batched_set(0, count=count, only=[k], n_median=med, sigma=sig)[0]
+    count, k, med, sig, mix, shift = a
+    return I.batched_set(0, count=count, only=[k], n_median=med, sigma=sig, mix=mix, shift=shift)[0]
 
 
-def batch_instances(count, positions, median, sigma, procs):
-    """The batch's problems at `positions`, built in `procs` spawned processes
-    (each problem has its own seed, so the result does not depend on procs)."""
-    from paper_2609_19557_gb300 import instances as I
-    if procs <= 1:
-        return I.batched_set(0, count=count, only=positions, n_median=median, sigma=sigma)
+def spawn_pool(procs):
+    """A pool of `procs` spawned processes whose numeric libraries run one
+    thread each (the variables are read when a child imports them; with one
+    BLAS thread pool per child the children oversubscribe the cores)."""
     import multiprocessing as mp
-    with mp.get_context("spawn").Pool(procs) as pool:
-        return pool.map(_batch_one, [(count, k, median, sigma) for k in positions], chunksize=1)
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        return mp.get_context("spawn").Pool(procs)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def batch_instances(count, positions, median, sigma, procs, mix="alternate"):
+    """The batch's problems at `positions`, built in `procs` spawned processes
+    (each problem has its own seed and the shift is computed once, so the
+    result does not depend on procs)."""
+    from paper_2609_19557_gb300 import instances as I
+    shift = I.batched_shift(0)
+    if procs <= 1:
+        return I.batched_set(0, count=count, only=positions, n_median=median, sigma=sigma, mix=mix, shift=shift)
+    with spawn_pool(procs) as pool:
+        return pool.map(_batch_one, [(count, k, median, sigma, mix, shift) for k in positions], chunksize=1)
 
 
 def run_batch(args):
@@ -499,7 +522,7 @@ def run_batch(args):
     P.load()
     t = time.perf_counter()
     insts = batch_instances(args.batch, batch_shard(args.batch, ws, rank), args.batch_median, args.batch_sigma,
-                            args.batch_procs)
+                            args.batch_procs, args.batch_mix)
     gen_s = time.perf_counter() - t
     t = time.perf_counter()
     hs = []
@@ -544,6 +567,22 @@ def run_batch(args):
             h.close()
         torch.distributed.destroy_process_group()
         return
+    whole_pool = None
+    if args.batch_compare and ws == 1:
+        hp = []
+        for inst in insts:
+            h = P.create_from_instance(inst, precision=args.precision)
+            P.pdnqp_set_param(h, "time_limit", args.batch_time_limit)
+            hp.append(h)
+        sts_p, wall_p = solve_all(hp, 0, args.batch_threads)
+        rp = [P.pdnqp_get(h)[2] for h in hp]
+        whole_pool = {"wall_s": wall_p, "solved": [P.STATUS_NAMES[x] for x in sts_p].count("SOLVED"),
+                      "inner_iters_total": int(sum(r["inner_iters"] for r in rp)),
+                      "same_iterates_as_fused": all(np.array_equal(P.pdnqp_get(a)[0], P.pdnqp_get(b)[0])
+                                                    for a, b in zip(hs, hp)),
+                      "fused_speedup": wall_p / wall}
+        for h in hp:
+            h.close()
     sub = hs[:8]
     t0 = time.perf_counter()
     for h in sub:
@@ -565,9 +604,11 @@ def run_batch(args):
            "generate_s": gen_s, "create_s": create_s,
            "first8": {"sequential_s": seq_s, "fused_s": fused_s, "thread_pool_s": pool_s,
                       "speedup_fused": seq_s / fused_s},
+           "whole_batch_thread_pool": whole_pool,
            "config": {"workload": f"{args.batch} independent nonconvex QPs: n lognormal (median {args.batch_median:g}, "
-                                  f"log-std {args.batch_sigma:g}) clipped to [1e3, 1e5]; half small generator "
-                                  "(m = n/2), half Motzkin-Straus G(n, 0.01)",
+                                  f"log-std {args.batch_sigma:g}) clipped to [1e3, 1e5]; "
+                                  + ("half small generator (m = n/2), half Motzkin-Straus G(n, 0.01)"
+                                     if args.batch_mix == "alternate" else "small generator (m = n/2)"),
                       "n_total": int(sum(ns)), "n_min": int(min(ns)), "n_max": int(max(ns)),
                       "n_scope": "rank 0 share" if ws > 1 else "whole batch",
                       "form": "fused: one captured graph, one launch per phase over all problems"}}

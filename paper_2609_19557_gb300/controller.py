@@ -51,9 +51,27 @@ def make_instances(specs, procs=0, pool=None):
         return pool.map(_make_args, specs, chunksize=1)
     if procs <= 1 or len(specs) < 2:
         return [make_instance(*sp) for sp in specs]
-    import multiprocessing as mp
-    with mp.get_context("spawn").Pool(procs) as pl:
+    with spawn_pool(procs) as pl:
         return pl.map(_make_args, specs, chunksize=1)
+
+
+def spawn_pool(procs):
+    """A pool of `procs` spawned processes (no copy of a CUDA context) whose
+    numeric libraries run one thread each: the variables are read when a
+    child imports them, and one BLAS thread pool per child would oversubscribe
+    the cores."""
+    import multiprocessing as mp
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        return mp.get_context("spawn").Pool(procs)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
 
 def create_all(insts, setup, threads=16):
@@ -80,10 +98,7 @@ def generate_batched(count, rng, n_min, n_max, *, eps, explore, time_limit, thre
     ns = [int(rng.integers(n_min, n_max + 1)) for _ in range(count)]
     shift = make_instance(10_000, ns[0])["shift"] if count else None
     data = []
-    pool = None
-    if procs > 1:
-        import multiprocessing as mp
-        pool = mp.get_context("spawn").Pool(procs)
+    pool = spawn_pool(procs) if procs > 1 else None
     t_start = time.perf_counter()
     for c0 in range(0, count, chunk):
         if time.perf_counter() - t_start > budget_s:

@@ -521,19 +521,29 @@ def svm_qp(seed: int = 101, n_target: int = 1_000_000) -> dict:
                  workload="svm", seed=seed, eta=eta, labels=y)
 
 
+def batched_shift(seed: int = 0) -> float:
+    """Diagonal shift shared by the small-generator problems of a batch: the
+    30 % eigenvalue quantile of an n = 2000 replica of its off-diagonal density."""
+    g = _rng(seed + 7919, WORKLOAD_CODES["batched"])
+    rep = _sym_offdiag(2000, g.integers(0, 2000, size=4000), g.integers(0, 2000, size=4000), g.standard_normal(4000))
+    return _quantile_shift(rep, 0.3)
+
+
 def batched_set(seed: int = 0, count: int = 256, n_lo: int = 1000, n_hi: int = 100_000,
-                n_median: float = 4000.0, sigma: float = 0.8, clique_p: float = 0.01, only=None) -> list:
+                n_median: float = 4000.0, sigma: float = 0.8, clique_p: float = 0.01, only=None,
+                mix: str = "alternate", shift: float = None) -> list:
     """A batch of independent problems of uneven sizes: n ~ lognormal (median
     n_median, log-std sigma, clipped to [n_lo, n_hi]); even positions use the
     small generator at that size with m = n / 2, odd positions Motzkin-Straus
-    QPs on G(n, clique_p).  Each problem has its own seed, so `only` (positions)
-    builds a subset identical to those positions of the whole batch."""
+    QPs on G(n, clique_p) (mix = "alternate"), or the small generator at every
+    position (mix = "small").  Each problem has its own seed, so `only`
+    (positions) builds a subset identical to those positions of the whole
+    batch."""
     rng = _rng(seed, WORKLOAD_CODES["batched"])
-    # One diagonal shift for the whole batch, from an n = 2000 replica of the
-    # small generator's off-diagonal density (30 % negative eigenvalues).
-    g = _rng(seed + 7919, WORKLOAD_CODES["batched"])
-    rep = _sym_offdiag(2000, g.integers(0, 2000, size=4000), g.integers(0, 2000, size=4000), g.standard_normal(4000))
-    shift = _quantile_shift(rep, 0.3)
+    # One diagonal shift for the whole batch (batched_shift; a caller that
+    # builds the batch in pieces computes it once and passes it).
+    if shift is None:
+        shift = batched_shift(seed)
     ns = np.clip(np.exp(np.log(n_median) + sigma * rng.standard_normal(count)), n_lo, n_hi).astype(np.int64)
     out = []
     keep = set(range(count)) if only is None else set(int(k) for k in only)
@@ -541,7 +551,7 @@ def batched_set(seed: int = 0, count: int = 256, n_lo: int = 1000, n_hi: int = 1
         if k not in keep:
             continue
         s = int(seed) * 100_003 + k
-        if k % 2 == 0:
+        if k % 2 == 0 or mix == "small":
             out.append(small_qp(s, n=int(n), m=int(n) // 2, shift=shift))
         else:
             out.append(clique_qp(s, n=int(n), p=clique_p))
