@@ -23,7 +23,7 @@ _lock = threading.Lock()
 _lib = None
 
 SNAP_SCALARS = 8
-CHK_COLS = 14
+CHK_COLS = 22
 OTR_COLS = 25
 STATUS = {0: "SOLVED", 1: "PRIMAL_INFEASIBLE", 2: "DUAL_INFEASIBLE", 3: "ITER_LIMIT", 4: "TIME_LIMIT",
           5: "NUMERICAL_ERROR"}
@@ -320,7 +320,8 @@ def debug_checks(inst: dict, max_checks: int, x0=None, **params):
     vecs = np.zeros((max_checks, 3 * (dw + P.m)))
     got = lib().or_debug_checks(P.ref(), C.byref(prm), int(max_checks), _ptr(rows), _ptr(vecs))
     names = ["t_total", "t", "k_cur", "k_avg", "k_restart", "k_last", "use_avg", "restart", "omega",
-             "omega_after", "kappa", "kappa_after", "t_after", "k_restart_after"]
+             "omega_after", "kappa", "kappa_after", "t_after", "k_restart_after", "rp_cur", "rd_cur", "sp_cur",
+             "sd_cur", "rp_avg", "rd_avg", "sp_avg", "sd_avg"]
     out = []
     for r, v in zip(rows[:max(got, 0)], vecs[:max(got, 0)]):
         d = dict(zip(names, r))

@@ -665,7 +665,7 @@ typedef struct {
   double *chk_rows, *chk_vecs;
 } dbg_t;
 
-#define CHK_COLS 14
+#define CHK_COLS 22
 
 typedef struct {
   long long trials, accepted, restarts;
@@ -803,6 +803,8 @@ static int inner_solve(const sqp_t *S, const or_params *prm, const double *z, co
         crow = D->chk_rows + (size_t)D->chk_n * CHK_COLS;
         crow[0] = (double)ttot; crow[1] = (double)t; crow[2] = kc; crow[3] = ka; crow[4] = k_restart;
         crow[5] = k_last; crow[6] = use_avg; crow[7] = do_restart; crow[8] = omega; crow[10] = kappa;
+        crow[14] = Rc.rp; crow[15] = Rc.rd; crow[16] = Rc.sp; crow[17] = Rc.sd;
+        crow[18] = Ra.rp; crow[19] = Ra.rd; crow[20] = Ra.sp; crow[21] = Ra.sd;
         double *cv = D->chk_vecs + (size_t)D->chk_n * 3 * (size_t)(dw + m);
         for (int i = 0; i < dw; ++i) { cv[i] = I.ew[i] * w[i]; cv[dw + m + i] = I.ew[i] * wb[i];
                                         cv[2 * (dw + m) + i] = I.ew[i] * wst[i]; }
@@ -1324,7 +1326,9 @@ int or_debug_inner(const or_problem *P, const or_params *prm, int n_ckpt, const 
  *   current point, [3] of the average, [4] KKT_w at the last restart, [5] at
  *   the previous check, [6] average chosen, [7] restart, [8] omega before,
  *   [9] omega after, [10] kappa before, [11] kappa after, [12] t after,
- *   [13] KKT_w at the last restart after the decision
+ *   [13] KKT_w at the last restart after the decision, [14..17] r_p, r_d,
+ *   s_p, s_d of Eqs. inner-residuals / inner-scales at the current point,
+ *   [18..21] the same at the average
  * and the vectors [w | y | wbar | ybar | w_start | y_start] (dw and m
  * entries each, inner-unscaled coordinates, rows E then I) before the
  * decision.  Returns the number of rows written, or -1 on a numerical error. */

@@ -36,3 +36,21 @@ def test_transitions_scores_and_deviations():
 def test_transitions_guard_zero_residual():
     out = CT.transitions(_trace([(1e-2, 0, (0, 0), (0, 0)), (0.0, 0, (0, 0), (0, 0))]))
     assert np.isfinite(out[0][2]) and out[0][2] > 0
+
+
+@pytest.mark.parametrize("d", [
+    [-1, -2, 3, -4, -5, -1, -1, 0],
+    [1] * 6 + [-1] * 6,
+    [-3] * 18 + [2] * 14,
+    [5, 7, 9],
+    [0, 0],
+])
+def test_sign_test_matches_binomial_test(d):
+    """The paired evaluation's exact two-sided sign test equals the exact binomial
+    test of the number of negative differences among the nonzero ones (p = 1/2)."""
+    st = pytest.importorskip("scipy.stats")
+    k, nn, p = CT.sign_test(d)
+    dd = np.asarray(d)
+    assert k == int((dd < 0).sum()) and nn == int((dd != 0).sum())
+    want = st.binomtest(k, nn, 0.5).pvalue if nn else 1.0
+    assert abs(p - want) < 1e-12, (p, want)

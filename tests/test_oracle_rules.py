@@ -13,6 +13,8 @@ fails here:
 * kkt_metric / restart test (Sec. 3.3 restart paragraph; PDLP's criteria,
   reading A5) -> test_restart_metric_matches_definition,
   test_restart_decision_follows_pdlp_criteria;
+* inner_residuals (Eqs. inner-residuals / inner-scales)
+  -> test_inner_residuals_match_definition;
 * primal-weight update (Eqs. primal-weight-movement / primal-weight-update)
   -> test_primal_weight_update;
 * inner-tolerance factor (Eq. inner-tolerance-factor, floor reading A14)
@@ -82,6 +84,25 @@ def test_restart_metric_matches_definition(checks):
         # relative 1e-9, plus rounding of B w - h and of the projected step (entries O(1))
         assert abs(c["k_cur"] - kc) <= 1e-9 * kc + 1e-12, (c["t_total"], c["k_cur"], kc)
         assert abs(c["k_avg"] - ka) <= 1e-9 * ka + 1e-12, (c["t_total"], c["k_avg"], ka)
+
+
+def test_inner_residuals_match_definition(checks):
+    """Eqs. inner-residuals / inner-scales at every check, for the current point
+    and the average, recomputed from the dense unscaled inner QP:
+    r_p = ||Bw - h||, r_d = ||w - P_W(w - H w - q + B'y)||, s_p = max(1, ||Bw||,
+    ||h||), s_d = max(1, ||Hw||, ||q||, ||B'y||) (all l_inf)."""
+    ck, _, qp = checks
+    H, q, B, h, lo, hi = qp["H"], qp["q"], qp["B"], qp["h"], qp["lo"], qp["hi"]
+    for c in ck:
+        for tag, w, y in (("cur", c["w"], c["y"]), ("avg", c["wbar"], c["ybar"])):
+            bw, hw, bty = B @ w, H @ w, B.T @ y
+            rp = np.abs(bw - h).max()
+            rd = np.abs(w - _proj(w - (hw + q - bty), lo, hi)).max()
+            sp_ = max(1.0, np.abs(bw).max(), np.abs(h).max())
+            sd = max(1.0, np.abs(hw).max(), np.abs(q).max(), np.abs(bty).max())
+            for name, want, scale in (("rp", rp, sp_), ("rd", rd, sd), ("sp", sp_, sp_), ("sd", sd, sd)):
+                got = c[f"{name}_{tag}"]
+                assert abs(got - want) <= 1e-12 * scale, (c["t_total"], name, tag, got, want)
 
 
 def test_restart_decision_follows_pdlp_criteria(checks):
